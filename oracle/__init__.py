@@ -1,0 +1,189 @@
+"""CPU oracle for balanced (p,q)-biclique counting.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline leg use it; the product path never imports it. It shares no code with
+the CUDA path.
+
+Two independent counters:
+
+* `count` -- Algorithm 2 (BBVP) of the paper, in plain C (`sbc_oracle.c`),
+  step for step in the paper's order.
+* `brute_count` -- the definition itself (Section 3, Definitions 1-4 and the
+  problem statement), in pure Python: every p-subset L of U and q-subset R of
+  V, kept when L x R is complete and every butterfly in it has an even number
+  of negative edges. Tiny graphs only.
+
+Convention (the problem statement takes p vertices from one partition and q
+from the other): p vertices come from U (the CSR rows) and q from V.
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import os
+import subprocess
+from math import comb
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sbc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libsbc_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc -O2 -fopenmp) into oracle/_build/."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-fopenmp", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC]
+        )
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _declare(lib):
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    lib.sbc_oracle_count.restype = ctypes.c_int
+    lib.sbc_oracle_count.argtypes = [
+        ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_void_p,
+        ctypes.c_void_p,
+    ]
+    lib.sbc_oracle_binom.restype = ctypes.c_int
+    lib.sbc_oracle_binom.argtypes = [ctypes.c_int64, ctypes.c_int, u64p]
+    lib.sbc_oracle_max_threads.restype = ctypes.c_int
+    return lib
+
+
+def mutant(n: int, outdir: str):
+    """A copy of the oracle with planted mistake `n` (see ORACLE_MUTANT in
+    sbc_oracle.c), for tests that show the pins catch it."""
+    path = os.path.join(outdir, f"libsbc_oracle_mutant{n}.so")
+    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-shared", "-fPIC",
+                           f"-DORACLE_MUTANT={n}", "-o", path, _SRC])
+    return _declare(ctypes.CDLL(path))
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        lib.sbc_oracle_count.restype = ctypes.c_int
+        lib.sbc_oracle_count.argtypes = [
+            ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_void_p,
+            ctypes.c_void_p,
+        ]
+        lib.sbc_oracle_binom.restype = ctypes.c_int
+        lib.sbc_oracle_binom.argtypes = [ctypes.c_int64, ctypes.c_int, u64p]
+        lib.sbc_oracle_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().sbc_oracle_max_threads())
+
+
+def default_side(n_u: int, n_v: int) -> int:
+    """Algorithm 2 anchors on the smaller partition S (ties: U). 0 = U, 1 = V."""
+    return 0 if n_u <= n_v else 1
+
+
+def _u128(lo, hi) -> int:
+    return int(lo) | (int(hi) << 64)
+
+
+def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
+          per_anchor: bool = False, with_tuples: bool = False, lib=None):
+    """Balanced (p,q)-bicliques of `g` (p from U, q from V) by Algorithm 2.
+
+    side: anchor partition S (0 = U with tuple size p, 1 = V with tuple size
+    q); default the smaller partition. threads: OpenMP threads (0 = all).
+    Returns the count (int); with per_anchor, also a list of each anchor's
+    contribution (indexed by vertex id of S); with with_tuples, also the
+    number of (|S-tuple|-1)-subsets of C enumerated.
+    """
+    lib = _load() if lib is None else lib
+    if side is None:
+        side = default_side(g.n_u, g.n_v)
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    col = np.ascontiguousarray(g.cols, dtype=np.int32)
+    sgn = np.ascontiguousarray(g.signs, dtype=np.int8)
+    out = (ctypes.c_uint64 * 2)()
+    tup = (ctypes.c_uint64 * 2)()
+    n_s = g.n_u if side == 0 else g.n_v
+    anc = np.zeros(2 * max(n_s, 1), dtype=np.uint64) if per_anchor else None
+    rc = lib.sbc_oracle_count(
+        g.n_u, g.n_v, off.ctypes.data, col.ctypes.data, sgn.ctypes.data, p, q, side, threads,
+        out, anc.ctypes.data if anc is not None else None, ctypes.addressof(tup),
+    )
+    if rc == 1:
+        raise OverflowError("balanced biclique count term exceeds 128 bits")
+    if rc != 0:
+        raise RuntimeError(f"oracle failed with code {rc}")
+    total = _u128(out[0], out[1])
+    res = [total]
+    if per_anchor:
+        res.append([_u128(anc[2 * i], anc[2 * i + 1]) for i in range(n_s)])
+    if with_tuples:
+        res.append(_u128(tup[0], tup[1]))
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def binom(n: int, k: int) -> int:
+    """The oracle's exact binomial (for pinning it against closed forms)."""
+    out = (ctypes.c_uint64 * 2)()
+    if _load().sbc_oracle_binom(n, k, out):
+        raise OverflowError("binomial exceeds 128 bits")
+    return _u128(out[0], out[1])
+
+
+def butterfly_balanced(s11: int, s12: int, s21: int, s22: int) -> bool:
+    """A butterfly is balanced when it has an even number of negative edges."""
+    return sum(1 for s in (s11, s12, s21, s22) if s < 0) % 2 == 0
+
+
+def brute_count(g, p: int, q: int) -> int:
+    """Count by the definition: complete L x R with no unbalanced butterfly."""
+    sign = {}
+    rows, cols, sg = g.edges()
+    for u, v, s in zip(rows.tolist(), cols.tolist(), sg.tolist()):
+        sign[(u, v)] = s
+    total = 0
+    for L in itertools.combinations(range(g.n_u), p):
+        common = None
+        for u in L:
+            nb = set(cols[g.offsets[u]:g.offsets[u + 1]].tolist())
+            common = nb if common is None else common & nb
+        if common is None or len(common) < q:
+            continue
+        for R in itertools.combinations(sorted(common), q):
+            ok = True
+            for (u1, u2) in itertools.combinations(L, 2):
+                for (v1, v2) in itertools.combinations(R, 2):
+                    if not butterfly_balanced(sign[(u1, v1)], sign[(u1, v2)],
+                                              sign[(u2, v1)], sign[(u2, v2)]):
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if ok:
+                total += 1
+    return total
+
+
+def unsigned_count(g, p: int, q: int) -> int:
+    """(p,q)-bicliques ignoring signs: sum over p-subsets L of U of
+    binom(|common neighbourhood of L|, q) (tiny graphs only)."""
+    total = 0
+    nbs = [set(g.cols[g.offsets[u]:g.offsets[u + 1]].tolist()) for u in range(g.n_u)]
+    for L in itertools.combinations(range(g.n_u), p):
+        common = set.intersection(*(nbs[u] for u in L))
+        total += comb(len(common), q)
+    return total

@@ -1,0 +1,293 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle (`oracle.count`, Algorithm 2 in C) and the brute force
+(`oracle.brute_count`, the definition of Section 3) are checked against facts
+that do not come from either: the butterflies of Figure 2, the worked example
+of Figure 3, a hand-derived count on Figure 1(b), closed forms on complete
+bipartite graphs, the (2,q) pair formula, exact binomials and invariances.
+Each pin is chosen so that a plausible slip (ties in the vertex priority, a
+wrong sign relation, a dropped binomial term, a transposed side) fails it.
+"""
+import itertools
+import random
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle
+import sbc_synth
+from golden_io import butterflies, expectations, graph
+
+
+def complete(m, n, sign_fn=lambda u, v: 1):
+    u, v = np.divmod(np.arange(m * n), n)
+    s = np.array([sign_fn(a, b) for a, b in zip(u.tolist(), v.tolist())], dtype=np.int8)
+    return sbc_synth.from_edges(m, n, u, v, s)
+
+
+def transpose(g):
+    u, v, s = g.edges()
+    return sbc_synth.from_edges(g.n_v, g.n_u, v, u, s)
+
+
+# --- Figure 2: butterfly parity --------------------------------------------
+
+@pytest.mark.parametrize("panel", butterflies(), ids=lambda b: b[0])
+def test_fig2_butterfly_parity(panel):
+    _, s11, s12, s21, s22, balanced = panel
+    assert oracle.butterfly_balanced(s11, s12, s21, s22) == balanced
+    g = sbc_synth.from_edges(2, 2, [0, 0, 1, 1], [0, 1, 0, 1], [s11, s12, s21, s22])
+    assert oracle.brute_count(g, 2, 2) == int(balanced)
+    for side in (0, 1):
+        assert oracle.count(g, 2, 2, side=side) == int(balanced)
+
+
+# --- Figure 3: worked example ------------------------------------------------
+
+def test_fig3_example_counts():
+    g = graph("fig3_example.txt", 4, 4)
+    # printed: balanced (3,3) = 0 (no triple has 3 common neighbours) for any
+    # signs; check the all-positive and random signings
+    rng = random.Random(3)
+    for trial in range(20):
+        signs = [1] * g.m if trial == 0 else [rng.choice((1, -1)) for _ in range(g.m)]
+        h = graph("fig3_example.txt", 4, 4, signs)
+        for side in (0, 1):
+            assert oracle.count(h, 3, 3, side=side) == 0
+        assert oracle.brute_count(h, 3, 3) == 0
+    # the printed triple intersections have size 2, so with all edges positive
+    # each of the three triples with u1 contributes binom(2,2) = 1, and
+    # {u2,u3,u4} shares only v1: (3,2) = 3
+    assert oracle.count(g, 3, 2, side=0) == 3
+    # printed candidate set: u2, u3, u4 each share 3 neighbours with u1, so
+    # with all edges positive the (2,3) count is 3 (one per pair (u1, ui));
+    # other pairs share at most 2 neighbours
+    assert oracle.count(g, 2, 3, side=0) == 3
+    assert oracle.count(g, 2, 3, side=1) == 3
+
+
+def test_fig3_per_anchor():
+    g = graph("fig3_example.txt", 4, 4)
+    # anchors are the lowest-priority vertex of their tuple; the (3,2) count of
+    # 3 all comes from tuples containing u1 (degree 4) and two of u2..u4
+    # (degree 3). The lowest-priority vertex of {u1,u2,u3} is u2 (degree 3,
+    # id 1 < id 2), etc.; per-anchor values must add up to the total.
+    total, per = oracle.count(g, 3, 2, side=0, per_anchor=True)
+    assert total == 3 and sum(per) == 3
+    assert per[0] == 0  # u1 has the highest priority, never an anchor here
+
+
+# --- Figure 1(b): hand-derived count ----------------------------------------
+
+def test_fig1b_hand_derived():
+    g = graph("fig1b_k44.txt", 4, 4)
+    for p, q, c in expectations("fig1b_k44.txt"):
+        assert oracle.brute_count(g, p, q) == c
+        assert oracle.count(g, p, q, side=0) == c
+        assert oracle.count(g, p, q, side=1) == c
+
+
+# --- closed forms on complete bipartite graphs ------------------------------
+
+@pytest.mark.parametrize("m,n", [(3, 3), (4, 5), (6, 4), (7, 7)])
+def test_complete_all_positive(m, n):
+    g = complete(m, n)
+    for p in range(2, min(m, 5) + 1):
+        for q in range(2, min(n, 5) + 1):
+            want = comb(m, p) * comb(n, q)
+            assert oracle.count(g, p, q, side=0) == want
+            assert oracle.count(g, p, q, side=1) == want
+            if m * n <= 30:
+                assert oracle.brute_count(g, p, q) == want
+
+
+@pytest.mark.parametrize("m,n,seed", [(5, 4, 1), (6, 6, 2), (8, 5, 3)])
+def test_complete_two_factions(m, n, seed):
+    # planted factions without flips are switching-equivalent to all positive
+    rng = random.Random(seed)
+    lu = [rng.choice((1, -1)) for _ in range(m)]
+    lv = [rng.choice((1, -1)) for _ in range(n)]
+    g = complete(m, n, lambda u, v: lu[u] * lv[v])
+    for p, q in [(2, 2), (3, 3), (2, 4), (4, 3)]:
+        want = comb(m, p) * comb(n, q)
+        assert oracle.count(g, p, q, side=0) == want
+        assert oracle.count(g, p, q, side=1) == want
+        assert oracle.brute_count(g, p, q) == want
+
+
+@pytest.mark.parametrize("m,n,us,vs", [(4, 4, 0, 0), (5, 6, 2, 3), (6, 5, 5, 4)])
+def test_complete_one_negative_edge(m, n, us, vs):
+    # every biclique holding both u* and v* has a butterfly (u*, u', v*, v')
+    # with exactly one negative edge; all others are balanced
+    g = complete(m, n, lambda u, v: -1 if (u, v) == (us, vs) else 1)
+    for p, q in [(2, 2), (3, 3), (2, 3), (3, 2), (4, 4)]:
+        want = comb(m, p) * comb(n, q) - comb(m - 1, p - 1) * comb(n - 1, q - 1)
+        assert oracle.count(g, p, q, side=0) == want
+        assert oracle.count(g, p, q, side=1) == want
+        assert oracle.brute_count(g, p, q) == want
+
+
+# --- (2,q): balanced bicliques through a vertex pair --------------------------
+
+def pair_formula(g, q):
+    """p = 2: the two rows agree (same sign) on a set A and disagree on a set B
+    of common neighbours; a column set is balanced iff it lies in A or in B."""
+    nb = [dict(zip(g.cols[g.offsets[u]:g.offsets[u + 1]].tolist(),
+                   g.signs[g.offsets[u]:g.offsets[u + 1]].tolist())) for u in range(g.n_u)]
+    total = 0
+    for a, b in itertools.combinations(range(g.n_u), 2):
+        common = set(nb[a]) & set(nb[b])
+        same = sum(1 for v in common if nb[a][v] == nb[b][v])
+        total += comb(same, q) + comb(len(common) - same, q)
+    return total
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pair_formula(seed):
+    g = sbc_synth.tiny_random(100 + seed, 12, 10, 0.6, 0.3)
+    for q in (2, 3, 4):
+        want = pair_formula(g, q)
+        assert oracle.count(g, 2, q, side=0) == want
+        assert oracle.count(g, 2, q, side=1) == want
+
+
+# --- brute force on random tiny graphs ---------------------------------------
+
+@pytest.mark.parametrize("seed", range(40))
+def test_brute_force_random_tiny(seed):
+    rng = random.Random(seed)
+    n_u, n_v = rng.randint(2, 7), rng.randint(2, 7)
+    g = sbc_synth.tiny_random(seed, n_u, n_v, rng.uniform(0.5, 1.0), rng.uniform(0.0, 0.5))
+    for p in range(2, 5):
+        for q in range(2, 5):
+            want = oracle.brute_count(g, p, q)
+            assert oracle.count(g, p, q, side=0) == want, (p, q)
+            assert oracle.count(g, p, q, side=1) == want, (p, q)
+
+
+def test_degree_ties_count_once():
+    # a regular graph: every vertex has the same degree, so the priority is
+    # decided by ids alone; a tie rule that admits rho(w) >= rho(u) would count
+    # tuples more than once
+    g = complete(5, 5)
+    assert oracle.count(g, 3, 3, side=0) == comb(5, 3) ** 2
+    cyc_u, cyc_v = [], []
+    for i in range(6):
+        for d in range(3):
+            cyc_u.append(i)
+            cyc_v.append((i + d) % 6)
+    g2 = sbc_synth.from_edges(6, 6, cyc_u, cyc_v, [1] * len(cyc_u))
+    for p, q in [(2, 2), (2, 3), (3, 2), (3, 3)]:
+        assert oracle.count(g2, p, q, side=0) == oracle.brute_count(g2, p, q)
+
+
+# --- invariances --------------------------------------------------------------
+
+def switched(g, side, x):
+    u, v, s = g.edges()
+    s = s.copy()
+    s[(u if side == 0 else v) == x] *= -1
+    return sbc_synth.from_edges(g.n_u, g.n_v, u, v, s)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_invariances_small_chung_lu(seed):
+    g = sbc_synth.chung_lu_signed(50 + seed, 60, 40, 600, 2.1, 2.1, 0.2)
+    for p, q in [(3, 3), (2, 3), (3, 4)]:
+        c = oracle.count(g, p, q, side=0)
+        assert oracle.count(g, p, q, side=1) == c
+        assert oracle.count(transpose(g), q, p, side=1) == c  # side swap
+        assert oracle.count(switched(g, 0, 3), p, q) == c  # switching at u
+        assert oracle.count(switched(g, 1, 5), p, q) == c  # switching at v
+        neg = sbc_synth.from_edges(g.n_u, g.n_v, *g.edges()[:2], -g.edges()[2])
+        assert oracle.count(neg, p, q) == c  # global negation
+        pu = np.random.default_rng(seed).permutation(g.n_u)
+        pv = np.random.default_rng(seed + 9).permutation(g.n_v)
+        u, v, s = g.edges()
+        relab = sbc_synth.from_edges(g.n_u, g.n_v, pu[u], pv[v], s)
+        assert oracle.count(relab, p, q) == c  # relabelling
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_all_positive_equals_unsigned(seed):
+    g = sbc_synth.tiny_random(200 + seed, 9, 9, 0.7, 0.0)
+    for p, q in [(2, 2), (3, 3), (3, 2), (4, 3)]:
+        assert oracle.count(g, p, q) == oracle.unsigned_count(g, p, q)
+
+
+def test_empty_and_degenerate():
+    g = sbc_synth.from_edges(5, 5, [], [], [])
+    assert oracle.count(g, 3, 3) == 0
+    g1 = sbc_synth.from_edges(1, 1, [0], [0], [1])
+    assert oracle.count(g1, 2, 2) == 0
+    star = sbc_synth.from_edges(1, 6, [0] * 6, list(range(6)), [1] * 6)
+    assert oracle.count(star, 2, 2) == 0
+
+
+# --- exact binomials -----------------------------------------------------------
+
+def test_binomials_exact():
+    for n in list(range(0, 40)) + [1000, 65535, 2**20 + 7, 2**31 - 1, 10**9]:
+        for k in range(0, 9):
+            want = comb(n, k)
+            if want.bit_length() <= 128:
+                assert oracle.binom(n, k) == want
+            else:
+                with pytest.raises(OverflowError):
+                    oracle.binom(n, k)
+    # beyond 64 bits, and right at the 128-bit edge
+    assert oracle.binom(2**40, 3) == comb(2**40, 3)
+    lo, hi = 8, 2**40  # largest n with binom(n, 8) < 2^128, by bisection
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        lo, hi = (mid, hi) if comb(mid, 8).bit_length() <= 128 else (lo, mid - 1)
+    n = lo
+    assert oracle.binom(n, 8) == comb(n, 8)
+    with pytest.raises(OverflowError):
+        oracle.binom(n + 1, 8)
+
+
+def test_tuples_metric_matches_candidate_sets():
+    # the enumerated (p-1)-subsets equal sum over anchors of binom(|C|, p-1);
+    # on K_{m,n} every higher-priority vertex is a candidate
+    m, n = 7, 5
+    g = complete(m, n)
+    _, tup = oracle.count(g, 3, 3, side=0, with_tuples=True)
+    assert tup == sum(comb(m - 1 - i, 2) for i in range(m))
+
+
+# --- the pins catch planted mistakes -------------------------------------------
+
+def _pins_pass(lib):
+    """Run a cross-section of the pins above against one oracle library."""
+    g = graph("fig1b_k44.txt", 4, 4)
+    for p, q, c in expectations("fig1b_k44.txt"):
+        for side in (0, 1):
+            if oracle.count(g, p, q, side=side, lib=lib) != c:
+                return False
+    for m, n, us, vs in [(5, 6, 2, 3)]:
+        h = complete(m, n, lambda u, v: -1 if (u, v) == (us, vs) else 1)
+        for p, q in [(2, 2), (3, 3), (3, 2)]:
+            want = comb(m, p) * comb(n, q) - comb(m - 1, p - 1) * comb(n - 1, q - 1)
+            for side in (0, 1):
+                if oracle.count(h, p, q, side=side, lib=lib) != want:
+                    return False
+    for seed in range(8):
+        t = sbc_synth.tiny_random(seed, 6, 6, 0.8, 0.3)
+        for p, q in [(2, 3), (3, 3), (3, 2)]:
+            want = oracle.brute_count(t, p, q)
+            for side in (0, 1):
+                if oracle.count(t, p, q, side=side, lib=lib) != want:
+                    return False
+    return True
+
+
+def test_pins_pass_on_oracle():
+    assert _pins_pass(None)
+
+
+@pytest.mark.parametrize("mutant", range(1, 7))
+def test_pins_catch_planted_mistakes(mutant, tmp_path):
+    lib = oracle.mutant(mutant, str(tmp_path))
+    assert not _pins_pass(lib)
