@@ -1,0 +1,192 @@
+/*
+ * sbc.h -- balanced (p,q)-biclique counting in signed bipartite graphs on one
+ * NVIDIA GB300 GPU (sm_103a).
+ *
+ * The operation: given a signed bipartite graph G = (U, V, E) (Section 3:
+ * every edge (u,v) carries a sign + or -), count the balanced
+ * (p,q)-bicliques: pairs (L, R) with L a p-subset of U, R a q-subset of V,
+ * every (l, r) in L x R an edge, and no butterfly (2x2 sub-biclique) of L x R
+ * with an odd number of negative edges (Definitions 1-4 and the problem
+ * statement, Section 3). p and q are both at least 2 (the problem statement
+ * excludes p = 1 and q = 1).
+ *
+ * Convention: p vertices are taken from U (the rows of the input CSR) and q
+ * from V (its column ids). The paper draws p from the anchor side S of
+ * Algorithm 2 (the smaller partition); that count is count(G^T, p, q) here
+ * when S = V, and count(G, p, q) = count(G^T, q, p) always holds.
+ *
+ * The counting method is Algorithm 2 of the paper (vertex-based pruning,
+ * Section 4.3) executed by CUDA kernels: anchors u with the lowest vertex
+ * priority (Definition 4) in their tuple, 2-hop counts cnt[w], the candidate
+ * filter cnt[w] >= q, (p-1)-subsets of candidates, signed p-wedge types
+ * (Section 4.2, Lemma 1) and sums of binom(x[type], q). All counts are exact
+ * unsigned 128-bit integers.
+ *
+ * Conventions of this interface:
+ *  - Every function returns an sbc_status; on a non-OK status,
+ *    sbc_last_error() gives a message for the calling thread. No function
+ *    aborts the process or throws across the ABI.
+ *  - "stream" arguments are cudaStream_t values passed as void*; NULL means
+ *    the legacy default stream. Host pointers are ordinary pageable or pinned
+ *    memory; device pointers must be on the current device.
+ *  - The library copies every input. The caller keeps ownership of its
+ *    buffers and may free them as soon as the call returns.
+ *  - Handles are owned by the caller and freed only by the *_destroy calls.
+ *  - All entry points work on the CUDA device that is current on the calling
+ *    thread; a graph must be used on the device it was created on.
+ *  - Device memory comes from cudaMallocAsync on the call's stream unless an
+ *    allocator is installed with sbc_set_allocator.
+ */
+#ifndef SBC_H
+#define SBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbc_graph sbc_graph;   /* opaque, immutable after creation */
+typedef struct sbc_server sbc_server; /* opaque request server */
+
+/* Unsigned 128-bit integer, little-endian limbs: value = lo + hi * 2^64. */
+typedef struct {
+    uint64_t lo, hi;
+} sbc_u128;
+
+typedef enum {
+    SBC_OK = 0,
+    SBC_E_INVAL = 1,       /* bad argument (NULL pointer, p or q out of range) */
+    SBC_E_GRAPH = 2,       /* malformed graph (offsets, column ids, signs, duplicates) */
+    SBC_E_NOMEM = 3,       /* device or host allocation failed */
+    SBC_E_CUDA = 4,        /* a CUDA call or kernel failed */
+    SBC_E_TIMEOUT = 5,     /* a bounded wait ran out */
+    SBC_E_BUSY = 6,        /* server admission refused (memory or slots) */
+    SBC_E_UNSUPPORTED = 7, /* feature not available on this device or build */
+    SBC_E_OVERFLOW = 8     /* the exact count does not fit 128 bits */
+} sbc_status;
+
+/* sbc_graph_create flags */
+#define SBC_OFFS_I64 (1u << 0)    /* row_offsets are int64_t (else int32_t) */
+#define SBC_SIGN_BITS (1u << 1)   /* signs are packed bits, 1 per edge in CSR
+                                     order, bit (e & 7) of byte e >> 3, set =
+                                     negative (else one int8_t per edge, +1/-1) */
+#define SBC_DEVICE_PTRS (1u << 2) /* row_offsets, cols and signs are device pointers */
+
+/*
+ * Build a device-resident graph from a signed CSR over U (Section 3's input
+ * model): row u lists the V-neighbours of u in cols[row_offsets[u] ..
+ * row_offsets[u+1]), with one sign per edge. Rows need not be sorted.
+ *   n_u, n_v     vertex counts (>= 0, each < 2^31)
+ *   nnz          number of edges (must equal row_offsets[n_u]; < 2^31)
+ *   row_offsets  n_u+1 entries, int32 or int64 (SBC_OFFS_I64), row_offsets[0] = 0,
+ *                non-decreasing
+ *   cols         nnz int32 column ids in [0, n_v)
+ *   signs        nnz int8 (+1 / -1), or ceil(nnz/8) bytes of packed bits
+ * The graph is validated on the device: offsets, column range, sign values
+ * and duplicate (u, v) pairs give SBC_E_GRAPH. The call returns after the
+ * graph is built (it synchronises `stream`). Empty graphs are allowed.
+ */
+sbc_status sbc_graph_create(sbc_graph **out, int64_t n_u, int64_t n_v, int64_t nnz,
+                            const void *row_offsets, const int32_t *cols, const void *signs,
+                            uint32_t flags, void *stream);
+
+/* Free a graph and its device memory (synchronises the device first). */
+sbc_status sbc_graph_destroy(sbc_graph *g);
+
+typedef struct {
+    int64_t n_u, n_v, nnz;
+    int64_t max_deg_u, max_deg_v;
+    /* 2-paths through the other side, sum over y of binom(deg(y), 2): the
+     * number of 2-hop visits of Algorithm 2 when anchoring on that side */
+    uint64_t wedges_anchor_u, wedges_anchor_v;
+    uint64_t device_bytes; /* device memory held by the graph now */
+} sbc_graph_info_t;
+
+sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
+
+/* Anchor side choice (Algorithm 2 anchors on a side S; see sbc_count_opts). */
+#define SBC_SIDE_AUTO (-1) /* the side with fewer 2-paths to visit (ties: U) */
+#define SBC_SIDE_U 0       /* anchors in U: tuples of p, q from V */
+#define SBC_SIDE_V 1       /* anchors in V: tuples of q, p from U */
+
+/* sbc_count_opts flags */
+#define SBC_COUNT_PAPER_TUPLES (1 << 0) /* also count the candidate sets of Algorithm 2
+                                           exactly as printed (cnt over every neighbour)
+                                           and report sum binom(|C(u)|, k-1) in
+                                           sbc_count_stats.anchor_tuples */
+
+typedef struct {
+    int32_t anchor_side;  /* SBC_SIDE_AUTO, SBC_SIDE_U or SBC_SIDE_V */
+    int32_t flags;        /* SBC_COUNT_* bits, 0 for a plain count */
+    /* optional per-anchor contributions, host memory, n_side entries indexed
+     * by vertex id of the anchor side (n_u or n_v entries), or NULL */
+    sbc_u128 *per_anchor;
+    /* first shard of anchors and number of shards: anchors with
+     * (rank of the anchor) % shard_count == shard are counted. 0/0 or 0/1 = all. */
+    int32_t shard, shard_count;
+} sbc_count_opts;
+
+typedef struct {
+    sbc_u128 count;         /* the balanced (p,q)-biclique count */
+    /* anchor tuples: sum over anchors u of binom(|C(u)|, k-1), k the tuple
+     * size on the anchor side. With SBC_COUNT_PAPER_TUPLES, C(u) is the
+     * candidate set of Algorithm 2 (cnt >= other-side size over all of
+     * Gamma(u)), i.e. the number of (p-1)-subsets the algorithm enumerates;
+     * without it, C(u) is the smaller set the kernels keep (cnt counted only
+     * over neighbours v that can close a tuple) */
+    sbc_u128 anchor_tuples;
+    uint64_t candidates;    /* sum over anchors of |C(u)| */
+    uint64_t wedges;        /* 2-hop entries visited */
+    uint64_t work_items;    /* tuple-phase work items launched */
+    int32_t anchor_side;    /* side used */
+    int32_t kernels;        /* kernel launches issued by the call */
+    float ms_prepare;       /* orientation build (first use of a side) + plan */
+    float ms_twohop;        /* 2-hop candidate kernel */
+    float ms_tuples;        /* tuple / type-count kernel */
+    float ms_total;
+} sbc_count_stats;
+
+/*
+ * Count balanced (p,q)-bicliques (p from U, q from V), 2 <= p, q <= 8.
+ * Writes the exact count to *out (host memory) and returns when it is known
+ * (synchronises `stream`). SBC_E_OVERFLOW if the count needs more than 128 bits.
+ */
+sbc_status sbc_count(const sbc_graph *g, int p, int q, sbc_u128 *out, void *stream);
+
+/* sbc_count with options (anchor side, per-anchor output, sharding) and
+ * statistics; opts and stats may be NULL. */
+sbc_status sbc_count_ex(const sbc_graph *g, int p, int q, const sbc_count_opts *opts,
+                        sbc_count_stats *stats, void *stream);
+
+/*
+ * One-call convenience for callers holding a host CSR: uploads the graph
+ * (sbc_graph_create with host pointers), counts, frees. Same arguments as
+ * sbc_graph_create followed by sbc_count.
+ */
+sbc_status sbc_count_csr(int64_t n_u, int64_t n_v, int64_t nnz, const void *row_offsets,
+                         const int32_t *cols, const void *signs, uint32_t flags, int p, int q,
+                         sbc_u128 *out, void *stream);
+
+/* Human-readable message for the last non-OK status on this thread. */
+const char *sbc_last_error(void);
+
+/* Library version string. */
+const char *sbc_version(void);
+
+/*
+ * Route the library's device allocations through caller functions (for
+ * example a framework's caching allocator). alloc returns a device pointer of
+ * at least `bytes` bytes usable on `stream`, or NULL; free releases it.
+ * Passing NULL functions restores cudaMallocAsync / cudaFreeAsync.
+ */
+typedef void *(*sbc_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*sbc_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+sbc_status sbc_set_allocator(sbc_alloc_fn alloc, sbc_free_fn free, void *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBC_H */

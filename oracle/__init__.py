@@ -51,7 +51,7 @@ def _declare(lib):
     lib.sbc_oracle_count.argtypes = [
         ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_void_p,
-        ctypes.c_void_p,
+        ctypes.c_void_p, ctypes.c_void_p,
     ]
     lib.sbc_oracle_binom.restype = ctypes.c_int
     lib.sbc_oracle_binom.argtypes = [ctypes.c_int64, ctypes.c_int, u64p]
@@ -71,18 +71,7 @@ def mutant(n: int, outdir: str):
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        u64p = ctypes.POINTER(ctypes.c_uint64)
-        lib.sbc_oracle_count.restype = ctypes.c_int
-        lib.sbc_oracle_count.argtypes = [
-            ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_void_p,
-            ctypes.c_void_p,
-        ]
-        lib.sbc_oracle_binom.restype = ctypes.c_int
-        lib.sbc_oracle_binom.argtypes = [ctypes.c_int64, ctypes.c_int, u64p]
-        lib.sbc_oracle_max_threads.restype = ctypes.c_int
-        _lib = lib
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
 
 
@@ -100,14 +89,15 @@ def _u128(lo, hi) -> int:
 
 
 def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
-          per_anchor: bool = False, with_tuples: bool = False, lib=None):
+          per_anchor: bool = False, with_tuples: bool = False, lib=None, anchors=None):
     """Balanced (p,q)-bicliques of `g` (p from U, q from V) by Algorithm 2.
 
     side: anchor partition S (0 = U with tuple size p, 1 = V with tuple size
     q); default the smaller partition. threads: OpenMP threads (0 = all).
     Returns the count (int); with per_anchor, also a list of each anchor's
     contribution (indexed by vertex id of S); with with_tuples, also the
-    number of (|S-tuple|-1)-subsets of C enumerated.
+    number of (|S-tuple|-1)-subsets of C enumerated. anchors: optional
+    iterable of S-vertex ids; only those anchors are processed.
     """
     lib = _load() if lib is None else lib
     if side is None:
@@ -119,9 +109,14 @@ def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
     tup = (ctypes.c_uint64 * 2)()
     n_s = g.n_u if side == 0 else g.n_v
     anc = np.zeros(2 * max(n_s, 1), dtype=np.uint64) if per_anchor else None
+    mask = None
+    if anchors is not None:
+        mask = np.zeros(max(n_s, 1), dtype=np.uint8)
+        mask[np.asarray(list(anchors), dtype=np.int64)] = 1
     rc = lib.sbc_oracle_count(
         g.n_u, g.n_v, off.ctypes.data, col.ctypes.data, sgn.ctypes.data, p, q, side, threads,
         out, anc.ctypes.data if anc is not None else None, ctypes.addressof(tup),
+        mask.ctypes.data if mask is not None else None,
     )
     if rc == 1:
         raise OverflowError("balanced biclique count term exceeds 128 bits")

@@ -212,8 +212,8 @@ typedef struct {
  * p = tuple size on S, q = size on the other side.
  */
 static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
-                uint64_t out[2], uint64_t *anchor_out, uint64_t *tuples_out,
-                int *ovf_out) {
+                const uint8_t *anchor_mask, uint64_t out[2], uint64_t *anchor_out,
+                uint64_t *tuples_out, int *ovf_out) {
     int64_t nS = s->n;
     int ovf = 0;
     int nt = 1;
@@ -263,6 +263,7 @@ static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
 #pragma omp for schedule(dynamic, 16)
         for (int64_t u = 0; u < nS; u++) {
             if (err) continue;
+            if (anchor_mask && !anchor_mask[u]) continue; /* test subset of anchors */
             u128 b_u = 0;       /* this anchor's contribution */
             u128 tuples_u = 0;  /* (p-1)-subsets of C enumerated */
             int64_t nt_touch = 0;
@@ -426,12 +427,15 @@ static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
  * off/col/sgn: CSR over U, signs +1/-1. out: u128 total as {lo, hi}.
  * anchor_out (optional): per-anchor contribution, 2 u64 per vertex of S.
  * tuples_out (optional): number of (p-1)-subsets enumerated, {lo, hi}.
+ * anchor_mask (optional): one byte per vertex of S; only anchors with a
+ * non-zero byte are processed (the total then covers those anchors only).
  * Returns 0, -1 on allocation failure, -2 on bad arguments, 1 on overflow.
  */
 int sbc_oracle_count(int64_t n_u, int64_t n_v, const int64_t *off,
                      const int32_t *col, const int8_t *sgn, int p_u, int q_v,
                      int anchor_side, int nthreads, uint64_t out[2],
-                     uint64_t *anchor_out, uint64_t *tuples_out) {
+                     uint64_t *anchor_out, uint64_t *tuples_out,
+                     const uint8_t *anchor_mask) {
     if (p_u < 2 || q_v < 2 || p_u > 16 || q_v > 16 || n_u < 0 || n_v < 0) return -2;
     side_t su, sv;
     memset(&su, 0, sizeof(su));
@@ -443,9 +447,9 @@ int sbc_oracle_count(int64_t n_u, int64_t n_v, const int64_t *off,
     }
     int ovf = 0, rc;
     if (anchor_side == 0)
-        rc = bbvp(&su, &sv, p_u, q_v, nthreads, out, anchor_out, tuples_out, &ovf);
+        rc = bbvp(&su, &sv, p_u, q_v, nthreads, anchor_mask, out, anchor_out, tuples_out, &ovf);
     else
-        rc = bbvp(&sv, &su, q_v, p_u, nthreads, out, anchor_out, tuples_out, &ovf);
+        rc = bbvp(&sv, &su, q_v, p_u, nthreads, anchor_mask, out, anchor_out, tuples_out, &ovf);
     free_side(&su);
     free_side(&sv);
     if (rc) return rc;

@@ -1,0 +1,285 @@
+"""Balanced (p,q)-biclique counting in signed bipartite graphs on GB300.
+
+Thin ctypes binding over libsbc.so (include/sbc.h): the same entry points,
+argument marshalling only. Every step of the count runs in the library's CUDA
+kernels; there is no CPU fallback, and importing this package fails loudly if
+the library has not been built (`paper_2605_03603_gb300.build.build()`).
+
+PyTorch is used only to hand over device memory and streams: device inputs
+may be torch CUDA tensors, and `stream` may be a torch.cuda.Stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "SbcError", "Graph", "sbc_graph_create", "sbc_graph_destroy", "sbc_graph_info",
+    "sbc_count", "sbc_count_ex", "sbc_count_csr", "sbc_last_error", "sbc_version",
+    "lib", "LIB_PATH",
+]
+
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libsbc.so is not built ({LIB_PATH}); run paper_2605_03603_gb300.build.build() "
+        "(nvcc for sm_103a) first. There is no CPU fallback."
+    )
+
+lib = ctypes.CDLL(LIB_PATH)
+
+SBC_OFFS_I64 = 1
+SBC_SIGN_BITS = 2
+SBC_DEVICE_PTRS = 4
+SBC_SIDE_AUTO, SBC_SIDE_U, SBC_SIDE_V = -1, 0, 1
+SBC_COUNT_PAPER_TUPLES = 1
+
+STATUS = {0: "SBC_OK", 1: "SBC_E_INVAL", 2: "SBC_E_GRAPH", 3: "SBC_E_NOMEM", 4: "SBC_E_CUDA",
+          5: "SBC_E_TIMEOUT", 6: "SBC_E_BUSY", 7: "SBC_E_UNSUPPORTED", 8: "SBC_E_OVERFLOW"}
+
+
+class U128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64)]
+
+    def value(self) -> int:
+        return int(self.lo) | (int(self.hi) << 64)
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n_u", ctypes.c_int64), ("n_v", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("max_deg_u", ctypes.c_int64), ("max_deg_v", ctypes.c_int64),
+                ("wedges_anchor_u", ctypes.c_uint64), ("wedges_anchor_v", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64)]
+
+
+class CountOpts(ctypes.Structure):
+    _fields_ = [("anchor_side", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("per_anchor", ctypes.c_void_p), ("shard", ctypes.c_int32),
+                ("shard_count", ctypes.c_int32)]
+
+
+class CountStats(ctypes.Structure):
+    _fields_ = [("count", U128), ("anchor_tuples", U128), ("candidates", ctypes.c_uint64),
+                ("wedges", ctypes.c_uint64), ("work_items", ctypes.c_uint64),
+                ("anchor_side", ctypes.c_int32), ("kernels", ctypes.c_int32),
+                ("ms_prepare", ctypes.c_float), ("ms_twohop", ctypes.c_float),
+                ("ms_tuples", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {"count": self.count.value(), "anchor_tuples": self.anchor_tuples.value(),
+                "candidates": int(self.candidates), "wedges": int(self.wedges),
+                "work_items": int(self.work_items), "anchor_side": int(self.anchor_side),
+                "kernels": int(self.kernels), "ms_prepare": float(self.ms_prepare),
+                "ms_twohop": float(self.ms_twohop), "ms_tuples": float(self.ms_tuples),
+                "ms_total": float(self.ms_total)}
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def _declare(name, restype, argtypes):
+    fn = getattr(lib, name)
+    fn.restype = restype
+    fn.argtypes = argtypes
+    return fn
+
+
+_declare("sbc_graph_create", ctypes.c_int,
+         [ctypes.POINTER(_vp), _i64, _i64, _i64, _vp, _vp, _vp, ctypes.c_uint32, _vp])
+_declare("sbc_graph_destroy", ctypes.c_int, [_vp])
+_declare("sbc_graph_info", ctypes.c_int, [_vp, ctypes.POINTER(GraphInfo)])
+_declare("sbc_count", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(U128), _vp])
+_declare("sbc_count_ex", ctypes.c_int,
+         [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(CountOpts), ctypes.POINTER(CountStats), _vp])
+_declare("sbc_count_csr", ctypes.c_int,
+         [_i64, _i64, _i64, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+          ctypes.POINTER(U128), _vp])
+_declare("sbc_last_error", ctypes.c_char_p, [])
+_declare("sbc_version", ctypes.c_char_p, [])
+
+
+class SbcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def sbc_last_error() -> str:
+    return lib.sbc_last_error().decode()
+
+
+def sbc_version() -> str:
+    return lib.sbc_version().decode()
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise SbcError(rc, sbc_last_error())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return getattr(stream, "cuda_stream", None)
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or torch tensor."""
+    if a is None:
+        return None, False
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, False
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), bool(getattr(a, "is_cuda", False))
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+class Graph:
+    """Owning handle of a device-resident graph (sbc_graph*)."""
+
+    def __init__(self, handle: int, n_u: int, n_v: int, nnz: int):
+        self.handle = handle
+        self.n_u, self.n_v, self.nnz = n_u, n_v, nnz
+
+    def close(self):
+        if self.handle:
+            _check(lib.sbc_graph_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sbc_graph_create(n_u: int, n_v: int, row_offsets, cols, signs, sign_bits: bool = False,
+                     stream=None) -> Graph:
+    """sbc_graph_create: signed CSR over U -> device graph.
+
+    row_offsets int32/int64, cols int32, signs int8 (+1/-1) or packed uint8
+    bits (sign_bits=True). numpy arrays are host memory; torch CUDA tensors are
+    device memory (all three must be on the same side)."""
+    off_p, off_dev = _ptr(row_offsets)
+    col_p, col_dev = _ptr(cols)
+    sg_p, sg_dev = _ptr(signs)
+    nnz = int(cols.shape[0])
+    flags = 0
+    dt = str(getattr(row_offsets, "dtype", ""))
+    if dt.endswith("int64"):
+        flags |= SBC_OFFS_I64
+    elif not dt.endswith("int32"):
+        raise TypeError("row_offsets must be int32 or int64")
+    if not str(getattr(cols, "dtype", "")).endswith("int32"):
+        raise TypeError("cols must be int32")
+    if sign_bits:
+        flags |= SBC_SIGN_BITS
+    if off_dev or col_dev or sg_dev:
+        if not (off_dev and (col_dev or nnz == 0) and (sg_dev or nnz == 0)):
+            raise ValueError("row_offsets, cols and signs must all be host or all be device")
+        flags |= SBC_DEVICE_PTRS
+    out = _vp()
+    _check(lib.sbc_graph_create(ctypes.byref(out), n_u, n_v, nnz, off_p, col_p, sg_p, flags,
+                                _stream_ptr(stream)))
+    return Graph(out.value, n_u, n_v, nnz)
+
+
+def sbc_graph_destroy(g: Graph):
+    g.close()
+
+
+def sbc_graph_info(g: Graph) -> dict:
+    info = GraphInfo()
+    _check(lib.sbc_graph_info(g.handle, ctypes.byref(info)))
+    return {f: int(getattr(info, f)) for f, _ in GraphInfo._fields_}
+
+
+def sbc_count(g: Graph, p: int, q: int, stream=None) -> int:
+    """Exact number of balanced (p,q)-bicliques (p from U, q from V)."""
+    out = U128()
+    _check(lib.sbc_count(g.handle, p, q, ctypes.byref(out), _stream_ptr(stream)))
+    return out.value()
+
+
+def sbc_count_ex(g: Graph, p: int, q: int, anchor_side: int = SBC_SIDE_AUTO,
+                 per_anchor: bool = False, paper_tuples: bool = False, shard: int = 0,
+                 shard_count: int = 0, stream=None):
+    """sbc_count_ex: returns (count, stats dict, per-anchor list or None)."""
+    opts = CountOpts()
+    opts.anchor_side = anchor_side
+    opts.flags = SBC_COUNT_PAPER_TUPLES if paper_tuples else 0
+    opts.shard = shard
+    opts.shard_count = shard_count
+    n_side = None
+    per = None
+    if per_anchor:
+        side = anchor_side
+        if side == SBC_SIDE_AUTO:
+            info = sbc_graph_info(g)
+            side = 0 if info["wedges_anchor_u"] <= info["wedges_anchor_v"] else 1
+            opts.anchor_side = side
+        n_side = g.n_u if side == 0 else g.n_v
+        per = np.zeros(2 * max(n_side, 1), dtype=np.uint64)
+        opts.per_anchor = per.ctypes.data
+    st = CountStats()
+    _check(lib.sbc_count_ex(g.handle, p, q, ctypes.byref(opts), ctypes.byref(st),
+                            _stream_ptr(stream)))
+    d = st.as_dict()
+    pa = None
+    if per is not None:
+        pa = [int(per[2 * i]) | (int(per[2 * i + 1]) << 64) for i in range(n_side)]
+    return d["count"], d, pa
+
+
+def sbc_count_csr(n_u: int, n_v: int, row_offsets, cols, signs, p: int, q: int,
+                  sign_bits: bool = False, stream=None) -> int:
+    """One call: host CSR in, exact count out (uploads, counts, frees)."""
+    off_p, off_dev = _ptr(row_offsets)
+    col_p, _ = _ptr(cols)
+    sg_p, _ = _ptr(signs)
+    flags = SBC_OFFS_I64 if str(row_offsets.dtype).endswith("int64") else 0
+    if sign_bits:
+        flags |= SBC_SIGN_BITS
+    if off_dev:
+        flags |= SBC_DEVICE_PTRS
+    out = U128()
+    _check(lib.sbc_count_csr(n_u, n_v, int(cols.shape[0]), off_p, col_p, sg_p, flags, p, q,
+                             ctypes.byref(out), _stream_ptr(stream)))
+    return out.value()
+
+
+def graph_from_synth(g, device: bool = False, sign_bits: bool = False, stream=None) -> Graph:
+    """Convenience: a sbc_synth.SignedBipartite to a device graph (host or
+    device-resident inputs)."""
+    signs = g.packed_sign_bits() if sign_bits else g.signs
+    if device:
+        import torch
+
+        off = torch.from_numpy(np.ascontiguousarray(g.offsets)).cuda()
+        col = torch.from_numpy(np.ascontiguousarray(g.cols)).cuda()
+        sg = torch.from_numpy(np.ascontiguousarray(signs)).cuda()
+        return sbc_graph_create(g.n_u, g.n_v, off, col, sg, sign_bits=sign_bits, stream=stream)
+    return sbc_graph_create(g.n_u, g.n_v, np.ascontiguousarray(g.offsets),
+                            np.ascontiguousarray(g.cols), np.ascontiguousarray(signs),
+                            sign_bits=sign_bits, stream=stream)

@@ -1,0 +1,1361 @@
+// Counting kernels: Algorithm 2 (BBVP, vertex-based pruning, Section 4.3) on
+// the device.
+//
+// Notation. The anchor side X plays S of Algorithm 2; its vertices are
+// renumbered by rank in the vertex priority rho (Definition 4). k is the tuple
+// size on X and l the size on the other side Y (k = p, l = q when X = U;
+// k = q, l = p when X = V); R = k - 1 partners join each anchor.
+//
+// Per anchor u (rank r):
+//   position j of u's list Gamma(u) = (v_0, v_1, ...) is "useful" when the
+//   suffix of v_j's list above r holds at least R entries: only then can v_j
+//   be a common neighbour of u and R partners of higher rank. Useful
+//   positions are numbered 0..d'-1 and become bit positions.
+//   2-hop step (Algorithm 2, cnt and L maps): for every useful position j and
+//   every w in the suffix of v_j: cnt[w] += 1, P_w[j] = 1 and
+//   D_w[j] = (sign(u,v_j) != sign(w,v_j)). P_w is L[w] as a bitmask over
+//   Gamma(u); D_w holds the type letter of Section 4.2 (set = d, clear = s).
+//   Candidate filter (Algorithm 2): C = { w : cnt[w] >= l }.
+//   Tuple step: every R-subset A of C with T = AND of P_w over A (nested
+//   pruning: a prefix whose T already has fewer than l bits is dropped, which
+//   drops only subsets with |T| < l). The type of v_j is the vector of D_w[j]
+//   over A; x[type] = popc(T AND the matching D / NOT D masks), and the
+//   anchor adds sum over types of binom(x[type], l).
+// Positions that are not useful can never be in T, so leaving them out of
+// cnt changes no term of the sum; the paper's own candidate set (counted
+// over all positions) is also computed on request to report the number of
+// subsets Algorithm 2 enumerates.
+#include <algorithm>
+#include <vector>
+
+#include "sbc_internal.cuh"
+
+namespace sbc {
+
+namespace {
+
+constexpr uint32_t VMASK = 0x7FFFFFFFu;
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------------ counters
+
+// Device-side scalars of one count.
+struct Counters {
+    unsigned long long total[2];       // u128 count
+    unsigned long long tuples_paper[2];// u128, sum binom(|C_paper|, R)
+    unsigned long long tuples_ours[2]; // u128, sum binom(|C'|, R)
+    unsigned long long candidates;     // sum |C'| (or |C_paper| in stats mode)
+    unsigned long long wedges;         // 2-hop entries visited
+    unsigned long long cost_total;     // tuple-phase cost estimate
+    unsigned int n_active;             // anchors with work
+    unsigned int head_a;               // 2-hop queue head
+    unsigned int head_b;               // tuple queue head
+    unsigned int n_items;
+    unsigned int err;                  // error bits
+    unsigned int pad;
+};
+
+enum : unsigned {
+    CERR_OVERFLOW = 1u,   // a binomial or the sum left 128 bits
+    CERR_RESERVE = 2u,    // candidate reservation exceeded (cannot happen)
+    CERR_HASH = 4u,       // 2-hop table overflow after all retries
+};
+
+// Thresholds: the largest x for which binom(x, l) is computed exactly in 64
+// bits by the multiplicative formula (index l, 0..8).
+__constant__ unsigned long long c_binom64_max[9];
+
+// ------------------------------------------------------------------ binomials
+
+__device__ __forceinline__ void div_u128_small(unsigned long long &lo, unsigned long long &hi,
+                                               unsigned d) {
+    unsigned long long qh = hi / d;
+    unsigned long long r = hi % d;
+    unsigned long long a = (r << 32) | (lo >> 32);
+    unsigned long long q1 = a / d;
+    r = a % d;
+    unsigned long long b = (r << 32) | (lo & 0xFFFFFFFFull);
+    unsigned long long q0 = b / d;
+    hi = qh;
+    lo = (q1 << 32) | q0;
+}
+
+// (lo, hi) *= m; returns false on 128-bit overflow.
+__device__ __forceinline__ bool mul_u128_u64(unsigned long long &lo, unsigned long long &hi,
+                                             unsigned long long m) {
+    unsigned long long l0 = lo * m;
+    unsigned long long c = __umul64hi(lo, m);
+    unsigned long long h0 = hi * m;
+    unsigned long long hh = __umul64hi(hi, m);
+    unsigned long long nh = h0 + c;
+    bool ovf = hh != 0 || nh < h0;
+    lo = l0;
+    hi = nh;
+    return !ovf;
+}
+
+__device__ __forceinline__ unsigned gcd_u32(unsigned a, unsigned b) {
+    while (b) {
+        unsigned t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+template <int L>
+__device__ __forceinline__ unsigned long long binom_u64(unsigned long long x) {
+    unsigned long long r = 1;
+#pragma unroll
+    for (int i = 1; i <= L; i++) r = r * (x - L + i) / (unsigned long long)i;
+    return r;
+}
+
+// acc += binom(x, l), exact. Sets CERR_OVERFLOW if the term needs > 128 bits.
+__device__ __noinline__ void binom_add_slow(U128 &acc, unsigned long long x, int l,
+                                            unsigned *err) {
+    unsigned long long lo = 1, hi = 0;
+    for (int i = 1; i <= l; i++) {
+        unsigned long long f = x - l + i;
+        unsigned g = gcd_u32((unsigned)(f % (unsigned)i), (unsigned)i);
+        if (g == 0) g = (unsigned)i;
+        div_u128_small(lo, hi, (unsigned)i / g);
+        if (!mul_u128_u64(lo, hi, f / g)) {
+            atomicOr(err, CERR_OVERFLOW);
+            return;
+        }
+    }
+    U128 t;
+    t.lo = lo;
+    t.hi = hi;
+    acc.add(t);
+}
+
+__device__ __forceinline__ void binom_add(U128 &acc, unsigned x, int l, unsigned *err) {
+    if ((int)x < l) return;
+    if (x > c_binom64_max[l]) {
+        binom_add_slow(acc, x, l, err);
+        return;
+    }
+    unsigned long long v;
+    switch (l) {
+        case 2: v = binom_u64<2>(x); break;
+        case 3: v = binom_u64<3>(x); break;
+        case 4: v = binom_u64<4>(x); break;
+        case 5: v = binom_u64<5>(x); break;
+        case 6: v = binom_u64<6>(x); break;
+        case 7: v = binom_u64<7>(x); break;
+        default: v = binom_u64<8>(x); break;
+    }
+    acc.add(v);
+}
+
+// ------------------------------------------------------------------ plan
+
+// Warp per anchor: useful positions, wedge counts, reservation, sort key.
+__global__ void k_plan(const int64_t *__restrict__ A_off, const uint32_t *__restrict__ A_ent,
+                       const uint32_t *__restrict__ A_pos, const int64_t *__restrict__ B_off,
+                       int64_t nX, int R, int l, int shard, int nshard, int stats,
+                       uint32_t *__restrict__ A_bit, uint32_t *__restrict__ dprime,
+                       unsigned long long *__restrict__ e_use, unsigned long long *__restrict__ e_all,
+                       uint32_t *__restrict__ rsv_c, int64_t *__restrict__ rsv_w,
+                       uint32_t *__restrict__ skey, uint32_t *__restrict__ sval,
+                       Counters *cnt) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int64_t r = warp; r < nX; r += nwarps) {
+        int64_t e0 = A_off[r], e1 = A_off[r + 1];
+        uint32_t dp = 0;
+        unsigned long long eu = 0, ea = 0;
+        for (int64_t b = e0; b < e1; b += 32) {
+            int64_t e = b + lane;
+            bool in = e < e1;
+            unsigned long long suf = 0;
+            if (in) {
+                uint32_t y = A_ent[e] & VMASK;
+                suf = (unsigned long long)(B_off[y + 1] - B_off[y] - (int64_t)A_pos[e] - 1);
+            }
+            bool useful = in && suf >= (unsigned long long)R;
+            uint32_t bal = __ballot_sync(FULL, useful);
+            if (in) A_bit[e] = useful ? dp + __popc(bal & lt) : EMPTY;
+            dp += __popc(bal);
+            eu += useful ? suf : 0ull;
+            ea += suf;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            eu += __shfl_xor_sync(FULL, eu, o);
+            ea += __shfl_xor_sync(FULL, ea, o);
+        }
+        if (lane == 0) {
+            bool mine = nshard <= 1 || (r % nshard) == shard;
+            int64_t d = e1 - e0;
+            bool act_count = dp >= (uint32_t)l && eu >= (unsigned long long)R * l;
+            bool act_stats = d >= l && ea >= (unsigned long long)R * l;
+            bool active = mine && (stats ? act_stats : act_count);
+            unsigned long long rc = 0;
+            if (active) {
+                rc = eu / (unsigned long long)l;  // each candidate owns >= l useful wedges
+                unsigned long long above = (unsigned long long)(nX - 1 - r);
+                rc = rc < above ? rc : above;
+            }
+            uint32_t W = (dp + 31) / 32;
+            dprime[r] = dp;
+            e_use[r] = eu;
+            e_all[r] = ea;
+            rsv_c[r] = (uint32_t)rc;
+            rsv_w[r] = (int64_t)(2ull * W * rc);
+            unsigned long long cost = stats ? ea : eu;
+            skey[r] = active ? 0xFFFFFFFEu - (uint32_t)(cost < 0xFFFFFFFEull ? cost : 0xFFFFFFFEull)
+                             : 0xFFFFFFFFu;
+            sval[r] = (uint32_t)r;
+            if (active) atomicAdd(&cnt->n_active, 1u);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) rsv_w[nX] = 0;
+}
+
+// ------------------------------------------------------------------ 2-hop
+
+constexpr int PA_THREADS = 256;
+constexpr int PA_HS_MAX = 4096;            // hash slots
+constexpr int PA_WCAP = PA_HS_MAX / 2;     // wedges per window (load factor <= 1/2)
+constexpr int PA_STAGE_WORDS = 8192;       // staged P/D words
+constexpr size_t PA_SMEM = PA_HS_MAX * 4 + PA_HS_MAX * 8 + PA_STAGE_WORDS * 4;
+
+__device__ __forceinline__ uint32_t slot_of(uint32_t w, int lg) {
+    return (w * 0x9E3779B1u) >> (32 - lg);
+}
+__device__ __forceinline__ uint32_t class_of(uint32_t w, int lg) {
+    return lg ? ((w * 0x85EBCA6Bu) ^ (w >> 15)) * 0xC2B2AE35u >> (32 - lg) : 0u;
+}
+
+// Visit every 2-hop entry of the anchor: all positions (stats pass) or only
+// the useful ones. fn(w, sdiff, bit, useful) runs for entries whose hash class
+// equals `cls` (lg_nw = log2 of the class count).
+template <typename F>
+__device__ __forceinline__ void visit_twohop(int64_t ebase, int d, bool useful_only, int lg_nw,
+                                             uint32_t cls, const uint32_t *__restrict__ A_ent,
+                                             const uint32_t *__restrict__ A_pos,
+                                             const uint32_t *__restrict__ A_bit,
+                                             const int64_t *__restrict__ B_off,
+                                             const uint32_t *__restrict__ B_ent, F fn) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int g = warp * 32; g < d; g += nw * 32) {
+        int j = g + lane;
+        int64_t start = 0;
+        uint32_t len = 0, su = 0, bit = EMPTY;
+        if (j < d) {
+            int64_t e = ebase + j;
+            uint32_t a = A_ent[e];
+            uint32_t y = a & VMASK;
+            su = a >> 31;
+            bit = A_bit[e];
+            start = B_off[y] + (int64_t)A_pos[e] + 1;
+            len = (uint32_t)(B_off[y + 1] - start);
+            if (useful_only && bit == EMPTY) len = 0;
+        }
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint32_t total = __shfl_sync(FULL, incl, 31);
+        uint32_t excl = incl - len;
+        for (uint32_t base = 0; base < total; base += 32) {
+            uint32_t idx = base + lane;
+            int s = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                uint32_t ex = __shfl_sync(FULL, excl, s + step);
+                if (ex <= idx) s += step;
+            }
+            long long st = __shfl_sync(FULL, (long long)start, s);
+            uint32_t exs = __shfl_sync(FULL, excl, s);
+            uint32_t sus = __shfl_sync(FULL, su, s);
+            uint32_t bits = __shfl_sync(FULL, bit, s);
+            if (idx < total) {
+                uint32_t ent = B_ent[st + (idx - exs)];
+                uint32_t w = ent & VMASK;
+                if (class_of(w, lg_nw) == cls) fn(w, sus ^ (ent >> 31), bits);
+            }
+        }
+    }
+}
+
+struct TwohopArgs {
+    const int64_t *A_off;
+    const uint32_t *A_ent, *A_pos, *A_bit;
+    const int64_t *B_off;
+    const uint32_t *B_ent;
+    const uint32_t *dprime;
+    const unsigned long long *e_use, *e_all;
+    const uint32_t *rsv_c;
+    const int64_t *pool_off;
+    const uint32_t *order;
+    uint32_t *pool;
+    uint32_t *ncand, *npaper;
+    Counters *cnt;
+    int l;
+};
+
+template <bool STATS>
+__global__ void __launch_bounds__(PA_THREADS) k_twohop(TwohopArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *keys = (uint32_t *)smem_raw;
+    unsigned long long *vals = (unsigned long long *)(smem_raw + PA_HS_MAX * 4);
+    uint32_t *stage = (uint32_t *)(smem_raw + PA_HS_MAX * 12);
+    __shared__ int s_item;
+    __shared__ unsigned s_ncw, s_paper, s_ovf;
+    const int tid = threadIdx.x;
+    const int l = a.l;
+    unsigned long long wedges = 0;
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(&a.cnt->head_a, 1u);
+        __syncthreads();
+        int item = s_item;
+        if (item >= (int)a.cnt->n_active) break;
+        const uint32_t r = a.order[item];
+        const int64_t ebase = a.A_off[r];
+        const int d = (int)(a.A_off[r + 1] - ebase);
+        const uint32_t W = (a.dprime[r] + 31) / 32;
+        const uint32_t rsv = a.rsv_c[r];
+        uint32_t *region = a.pool + a.pool_off[r];
+        const unsigned long long e_vis = STATS ? a.e_all[r] : a.e_use[r];
+        int lg_nw = 0;
+        while (((unsigned long long)PA_WCAP << lg_nw) < e_vis) lg_nw++;
+        uint32_t nc = 0, npaper = 0;
+        for (int attempt = 0; attempt < 8; attempt++) {
+            const uint32_t nw = 1u << lg_nw;
+            unsigned long long per = (e_vis + nw - 1) >> lg_nw;
+            int lg_hs = 6;
+            while ((1ull << lg_hs) < 2 * per && lg_hs < 12) lg_hs++;
+            const uint32_t hs = 1u << lg_hs;
+            nc = 0;
+            npaper = 0;
+            bool restart = false;
+            for (uint32_t cls = 0; cls < nw; cls++) {
+                for (uint32_t i = tid; i < hs; i += PA_THREADS) {
+                    keys[i] = EMPTY;
+                    vals[i] = 0;
+                }
+                if (tid == 0) {
+                    s_ncw = 0;
+                    s_paper = 0;
+                    s_ovf = 0;
+                }
+                __syncthreads();
+                // pass 1: cnt[w] (low word: all positions, high word: useful)
+                visit_twohop(ebase, d, !STATS, lg_nw, cls, a.A_ent, a.A_pos, a.A_bit, a.B_off,
+                             a.B_ent, [&](uint32_t w, uint32_t, uint32_t bit) {
+                                 uint32_t sl = slot_of(w, lg_hs);
+                                 uint32_t probes = 0;
+                                 for (;;) {
+                                     uint32_t k = keys[sl];
+                                     if (k == w) break;
+                                     if (k == EMPTY) {
+                                         uint32_t old = atomicCAS(&keys[sl], EMPTY, w);
+                                         if (old == EMPTY || old == w) break;
+                                     }
+                                     sl = (sl + 1) & (hs - 1);
+                                     if (++probes >= hs) {
+                                         s_ovf = 1;
+                                         return;
+                                     }
+                                 }
+                                 atomicAdd(&vals[sl], bit != EMPTY ? 0x100000001ull : 1ull);
+                             });
+                __syncthreads();
+                if (s_ovf) {
+                    restart = true;
+                    break;
+                }
+                // candidate filter: cnt[w] >= l
+                for (uint32_t i = tid; i < hs; i += PA_THREADS) {
+                    if (keys[i] == EMPTY) continue;
+                    unsigned long long v = vals[i];
+                    if (STATS && (uint32_t)v >= (uint32_t)l) atomicAdd(&s_paper, 1u);
+                    if ((uint32_t)(v >> 32) >= (uint32_t)l) {
+                        uint32_t idx = atomicAdd(&s_ncw, 1u);
+                        vals[i] = (1ull << 63) | idx;
+                    } else {
+                        vals[i] = 0;
+                    }
+                }
+                __syncthreads();
+                const uint32_t ncw = s_ncw;
+                npaper += s_paper;
+                if (ncw > 0) {
+                    if (nc + ncw > rsv) {
+                        if (tid == 0) atomicOr(&a.cnt->err, CERR_RESERVE);
+                        __syncthreads();
+                        break;
+                    }
+                    const bool staged = 2ull * W * ncw <= (unsigned long long)PA_STAGE_WORDS;
+                    uint32_t *bits_base = staged ? stage : region + nc;
+                    const uint32_t bstride = staged ? ncw : rsv;
+                    for (uint32_t i = tid; i < 2 * W * ncw; i += PA_THREADS) {
+                        uint32_t wd = i / ncw, c = i % ncw;
+                        bits_base[(size_t)wd * bstride + c] = 0;
+                    }
+                    __syncthreads();
+                    // pass 2: P_w and D_w bits of candidates (useful positions)
+                    visit_twohop(ebase, d, true, lg_nw, cls, a.A_ent, a.A_pos, a.A_bit, a.B_off,
+                                 a.B_ent, [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                                     uint32_t sl = slot_of(w, lg_hs);
+                                     for (uint32_t probes = 0; probes < hs; probes++) {
+                                         uint32_t k = keys[sl];
+                                         if (k == w) {
+                                             unsigned long long v = vals[sl];
+                                             if (v >> 63) {
+                                                 uint32_t c = (uint32_t)v;
+                                                 uint32_t m = 1u << (bit & 31);
+                                                 size_t wd = bit >> 5;
+                                                 atomicOr(&bits_base[wd * bstride + c], m);
+                                                 if (sdiff)
+                                                     atomicOr(&bits_base[(W + wd) * bstride + c], m);
+                                             }
+                                             return;
+                                         }
+                                         if (k == EMPTY) return;
+                                         sl = (sl + 1) & (hs - 1);
+                                     }
+                                 });
+                    __syncthreads();
+                    if (staged) {
+                        for (uint32_t i = tid; i < 2 * W * ncw; i += PA_THREADS) {
+                            uint32_t wd = i / ncw, c = i % ncw;
+                            region[(size_t)wd * rsv + nc + c] = stage[i];
+                        }
+                    }
+                    nc += ncw;
+                }
+                __syncthreads();
+            }
+            if (!restart) break;
+            lg_nw++;
+            if (attempt == 7 && tid == 0) atomicOr(&a.cnt->err, CERR_HASH);
+            __syncthreads();
+        }
+        if (tid == 0) {
+            a.ncand[r] = nc;
+            if (STATS) a.npaper[r] = npaper;
+        }
+        if (tid == 0) wedges += e_vis;
+        __syncthreads();
+    }
+    if (tid == 0 && wedges) atomicAdd(&a.cnt->wedges, wedges);
+}
+
+// ------------------------------------------------------------------ items
+
+// Saturating binom(n, k) in 64 bits (planning cost only).
+__device__ __forceinline__ unsigned long long binom_sat(unsigned long long n, int k) {
+    if ((long long)n < k) return 0;
+    unsigned long long r = 1;
+    for (int i = 1; i <= k; i++) {
+        unsigned long long f = n - k + i;
+        if (r > 0xFFFFFFFFFFFFFFFFull / f) return 0xFFFFFFFFFFFFFFFFull;
+        r = r * f / i;
+    }
+    return r;
+}
+
+struct Item {
+    uint32_t anchor, i0, i1, u0, u1;  // u1 == 0: all units of rows [i0, i1)
+};
+
+constexpr int ROWS_MAX = 1024;
+
+struct ItemArgs {
+    const uint32_t *ncand, *npaper, *dprime;
+    int64_t nX;
+    int R;
+    unsigned long long item_cost;
+    const int64_t *item_off;  // emit pass
+    int64_t *item_cnt;        // count pass (nX + 1 entries)
+    Item *items;
+    uint32_t *ikey, *ival;
+    Counters *cnt;
+};
+
+__device__ __forceinline__ unsigned long long row_cost(uint32_t nc, uint32_t i, int R, uint32_t W) {
+    if (R == 1) return 0;
+    unsigned long long t = binom_sat(nc - 1 - i, R - 1);
+    unsigned long long c = t * W;
+    return (W && c / W != t) ? 0xFFFFFFFFFFFFFFFFull : c;
+}
+
+__device__ __forceinline__ unsigned long long unit_cost(uint32_t nc, uint32_t i, uint32_t u, int R,
+                                                        uint32_t W) {
+    if (R <= 2) return 32ull * W;
+    unsigned long long s = 0;
+    uint32_t j0 = i + 1 + 32 * u;
+    for (uint32_t j = j0; j < j0 + 32 && j < nc; j++) {
+        unsigned long long t = binom_sat(nc - 1 - j, R - 2);
+        s = (s + t < s) ? 0xFFFFFFFFFFFFFFFFull : s + t;
+    }
+    unsigned long long c = s * W;
+    return (W && c / W != s) ? 0xFFFFFFFFFFFFFFFFull : c;
+}
+
+// Anchor cost, anchor tuple counts. Thread per anchor.
+__global__ void k_anchor_cost(ItemArgs a) {
+    U128 tp, to;
+    unsigned long long cand = 0, cost = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.nX;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t nc = a.ncand[r];
+        uint32_t W = (a.dprime[r] + 31) / 32;
+        if (a.npaper) {
+            uint32_t np = a.npaper[r];
+            cand += np;
+            if (np >= (uint32_t)a.R) {
+                // binom(np, R) exactly: np < 2^32, R <= 7, fits 128 bits
+                unsigned long long lo = 1, hi = 0;
+                for (int i = 1; i <= a.R; i++) {
+                    unsigned long long f = np - a.R + i;
+                    unsigned g = gcd_u32((unsigned)(f % (unsigned)i), (unsigned)i);
+                    if (g == 0) g = i;
+                    div_u128_small(lo, hi, i / g);
+                    mul_u128_u64(lo, hi, f / g);
+                }
+                U128 t;
+                t.lo = lo;
+                t.hi = hi;
+                tp.add(t);
+            }
+        } else {
+            cand += nc;
+        }
+        if (nc >= (uint32_t)a.R) {
+            unsigned long long t = binom_sat(nc, a.R);
+            to.add(t);
+            unsigned long long c = t * (W ? W : 1);
+            cost = (cost + c < cost) ? 0xFFFFFFFFFFFFFFFFull : cost + c;
+        }
+    }
+    tp = warp_sum_u128(tp);
+    to = warp_sum_u128(to);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cand += __shfl_xor_sync(FULL, cand, o);
+        unsigned long long t = __shfl_xor_sync(FULL, cost, o);
+        cost = (cost + t < cost) ? 0xFFFFFFFFFFFFFFFFull : cost + t;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_add_u128(a.cnt->tuples_paper, tp.lo, tp.hi);
+        atomic_add_u128(a.cnt->tuples_ours, to.lo, to.hi);
+        atomicAdd(&a.cnt->candidates, cand);
+        atomicAdd(&a.cnt->cost_total, cost);
+    }
+}
+
+// Split each anchor's tuple space into items. EMIT == false counts them.
+template <bool EMIT>
+__global__ void k_items(ItemArgs a) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.nX;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t nc = a.ncand[r];
+        const int R = a.R;
+        int64_t n = 0;
+        int64_t out = EMIT ? a.item_off[r] : 0;
+        const uint32_t W = (a.dprime[r] + 31) / 32;
+        auto emit = [&](uint32_t i0, uint32_t i1, uint32_t u0, uint32_t u1, unsigned long long c) {
+            if (EMIT) {
+                Item it;
+                it.anchor = (uint32_t)r;
+                it.i0 = i0;
+                it.i1 = i1;
+                it.u0 = u0;
+                it.u1 = u1;
+                a.items[out + n] = it;
+                uint32_t c32 = c < 0xFFFFFFFEull ? (uint32_t)c : 0xFFFFFFFEu;
+                a.ikey[out + n] = 0xFFFFFFFEu - c32;
+                a.ival[out + n] = (uint32_t)(out + n);
+            }
+            n++;
+        };
+        if (nc >= (uint32_t)R && nc > 0) {
+            if (R == 1) {
+                uint32_t units = (nc + 31) / 32;
+                unsigned long long per = 32ull * W, acc = 0;
+                uint32_t u0 = 0;
+                for (uint32_t u = 0; u < units; u++) {
+                    if (acc > 0 && acc + per > a.item_cost) {
+                        emit(0, 1, u0, u, acc);
+                        u0 = u;
+                        acc = 0;
+                    }
+                    acc += per;
+                }
+                emit(0, 1, u0, units, acc);
+            } else {
+                const uint32_t rows = nc - R + 1;
+                uint32_t rb = 0;
+                unsigned long long acc = 0;
+                for (uint32_t i = 0; i < rows; i++) {
+                    unsigned long long ci = row_cost(nc, i, R, W);
+                    if (ci > a.item_cost) {
+                        if (i > rb) emit(rb, i, 0, 0, acc);
+                        uint32_t units = (nc - 1 - i + 31) / 32;
+                        uint32_t u0 = 0;
+                        unsigned long long ua = 0;
+                        for (uint32_t u = 0; u < units; u++) {
+                            unsigned long long cu = unit_cost(nc, i, u, R, W);
+                            if (ua > 0 && ua + cu > a.item_cost) {
+                                emit(i, i + 1, u0, u, ua);
+                                u0 = u;
+                                ua = 0;
+                            }
+                            ua = (ua + cu < ua) ? 0xFFFFFFFFFFFFFFFFull : ua + cu;
+                        }
+                        emit(i, i + 1, u0, units, ua);
+                        rb = i + 1;
+                        acc = 0;
+                    } else {
+                        if (i > rb && (acc + ci > a.item_cost || i - rb >= (uint32_t)ROWS_MAX)) {
+                            emit(rb, i, 0, 0, acc);
+                            rb = i;
+                            acc = 0;
+                        }
+                        acc += ci;
+                    }
+                }
+                if (rows > rb) emit(rb, rows, 0, 0, acc);
+            }
+        }
+        if (!EMIT) a.item_cnt[r] = n;
+    }
+    if (!EMIT && blockIdx.x == 0 && threadIdx.x == 0) a.item_cnt[a.nX] = 0;
+}
+
+// ------------------------------------------------------------------ tuples
+
+constexpr int PB_THREADS = 256;
+constexpr int PB_WARPS = PB_THREADS / 32;
+constexpr int PB_SMEM_WORDS = 24576;  // 96 KB of staged P/D words
+constexpr size_t PB_SMEM = PB_SMEM_WORDS * 4;
+
+struct TupleArgs {
+    const uint32_t *ncand, *dprime, *rsv_c;
+    const int64_t *pool_off;
+    const uint32_t *pool;
+    const Item *items;
+    const uint32_t *iorder;
+    Counters *cnt;
+    unsigned long long *per_anchor;  // u128 per anchor rank, or null
+    uint32_t *wide_scratch;          // per warp: R * wmax words
+    uint32_t wmax;
+    int l;
+};
+
+// View of an anchor's candidate masks: P(w, c) and D(w, c).
+struct Masks {
+    const uint32_t *base;
+    uint32_t stride, W, nc;
+    __device__ __forceinline__ uint32_t P(uint32_t w, uint32_t c) const {
+        return base[(size_t)w * stride + c];
+    }
+    __device__ __forceinline__ uint32_t D(uint32_t w, uint32_t c) const {
+        return base[(size_t)(W + w) * stride + c];
+    }
+};
+
+// Type counts of a tuple and the binomial sum. T: the lane's common
+// neighbourhood mask; idx[0..R-1]: the tuple's candidate indices.
+template <int R, int WN>
+__device__ __forceinline__ void leaf_narrow(const Masks &m, const uint32_t (&T)[WN],
+                                            const uint32_t (&idx)[R], int l, U128 &acc,
+                                            unsigned *err) {
+    if constexpr (R <= 3) {
+        uint32_t x[1 << R];
+#pragma unroll
+        for (int k = 0; k < (1 << R); k++) x[k] = 0;
+#pragma unroll
+        for (int w = 0; w < WN; w++) {
+            if (w >= (int)m.W) break;
+            uint32_t dd[R];
+#pragma unroll
+            for (int i = 0; i < R; i++) dd[i] = m.D(w, idx[i]);
+#pragma unroll
+            for (int k = 0; k < (1 << R); k++) {
+                uint32_t msk = T[w];
+#pragma unroll
+                for (int i = 0; i < R; i++) msk &= ((k >> i) & 1) ? dd[i] : ~dd[i];
+                x[k] += __popc(msk);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < (1 << R); k++) binom_add(acc, x[k], l, err);
+    } else {
+        // split T by each partner's type letter, dropping parts below l
+        uint32_t stk[R + 1][WN];
+        int lev[R + 1];
+        int sp = 0;
+#pragma unroll
+        for (int w = 0; w < WN; w++) stk[0][w] = T[w];
+        lev[0] = 0;
+        sp = 1;
+        while (sp > 0) {
+            sp--;
+            int lv = lev[sp];
+            uint32_t cur[WN];
+#pragma unroll
+            for (int w = 0; w < WN; w++) cur[w] = stk[sp][w];
+            if (lv == R) {
+                uint32_t n = 0;
+#pragma unroll
+                for (int w = 0; w < WN; w++) n += __popc(cur[w]);
+                binom_add(acc, n, l, err);
+                continue;
+            }
+            uint32_t a0[WN], a1[WN];
+            uint32_t n0 = 0, n1 = 0;
+#pragma unroll
+            for (int w = 0; w < WN; w++) {
+                uint32_t dw = (w < (int)m.W) ? m.D(w, idx[lv]) : 0u;
+                a0[w] = cur[w] & ~dw;
+                a1[w] = cur[w] & dw;
+                n0 += __popc(a0[w]);
+                n1 += __popc(a1[w]);
+            }
+            if ((int)n0 >= l) {
+#pragma unroll
+                for (int w = 0; w < WN; w++) stk[sp][w] = a0[w];
+                lev[sp] = lv + 1;
+                sp++;
+            }
+            if ((int)n1 >= l) {
+#pragma unroll
+                for (int w = 0; w < WN; w++) stk[sp][w] = a1[w];
+                lev[sp] = lv + 1;
+                sp++;
+            }
+        }
+    }
+}
+
+// Extend a warp-uniform prefix (mask `pre`, indices idx[0..L-2]) by every
+// candidate m >= start, lanes over m.
+template <int L, int R, int WN>
+__device__ void expand_narrow(const Masks &m, const uint32_t (&pre)[WN], uint32_t (&idx)[R],
+                              uint32_t start, int l, U128 &acc, unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t mb = start; mb < m.nc; mb += 32) {
+        uint32_t c = mb + lane;
+        bool valid = c < m.nc;
+        uint32_t T[WN];
+        uint32_t n = 0;
+#pragma unroll
+        for (int w = 0; w < WN; w++) {
+            T[w] = (valid && w < (int)m.W) ? (pre[w] & m.P(w, c)) : 0u;
+            n += __popc(T[w]);
+        }
+        if constexpr (L == R) {
+            if (valid && (int)n >= l) {
+                uint32_t id2[R];
+#pragma unroll
+                for (int i = 0; i < R; i++) id2[i] = idx[i];
+                id2[R - 1] = c;
+                leaf_narrow<R, WN>(m, T, id2, l, acc, err);
+            }
+        } else {
+            bool ok = valid && (int)n >= l && (m.nc - 1 - c) >= (uint32_t)(R - L);
+            uint32_t bal = __ballot_sync(FULL, ok);
+            while (bal) {
+                int s = __ffs(bal) - 1;
+                bal &= bal - 1;
+                uint32_t Ts[WN];
+#pragma unroll
+                for (int w = 0; w < WN; w++) Ts[w] = __shfl_sync(FULL, T[w], s);
+                idx[L - 1] = mb + s;
+                expand_narrow<L + 1, R, WN>(m, Ts, idx, mb + s + 1, l, acc, err);
+            }
+        }
+    }
+}
+
+// One work unit: row i (first partner) and a chunk of 32 second partners;
+// for R == 1 a chunk of 32 single partners.
+template <int R, int WN>
+__device__ void unit_narrow(const Masks &m, uint32_t i, uint32_t jc, int l, U128 &acc,
+                            unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    if constexpr (R == 1) {
+        uint32_t c = jc * 32 + lane;
+        if (c < m.nc) {
+            uint32_t T[WN];
+            uint32_t n = 0;
+#pragma unroll
+            for (int w = 0; w < WN; w++) {
+                T[w] = (w < (int)m.W) ? m.P(w, c) : 0u;
+                n += __popc(T[w]);
+            }
+            if ((int)n >= l) {
+                uint32_t id[1] = {c};
+                leaf_narrow<1, WN>(m, T, id, l, acc, err);
+            }
+        }
+    } else {
+        uint32_t Pi[WN];
+#pragma unroll
+        for (int w = 0; w < WN; w++) Pi[w] = (w < (int)m.W) ? m.P(w, i) : 0u;
+        uint32_t j = i + 1 + jc * 32 + lane;
+        bool valid = j < m.nc;
+        uint32_t T[WN];
+        uint32_t n = 0;
+#pragma unroll
+        for (int w = 0; w < WN; w++) {
+            T[w] = valid ? (Pi[w] & ((w < (int)m.W) ? m.P(w, j) : 0u)) : 0u;
+            n += __popc(T[w]);
+        }
+        if constexpr (R == 2) {
+            if (valid && (int)n >= l) {
+                uint32_t id[2] = {i, j};
+                leaf_narrow<2, WN>(m, T, id, l, acc, err);
+            }
+        } else {
+            bool ok = valid && (int)n >= l && (m.nc - 1 - j) >= (uint32_t)(R - 2);
+            uint32_t bal = __ballot_sync(FULL, ok);
+            uint32_t idx[R];
+            idx[0] = i;
+            while (bal) {
+                int s = __ffs(bal) - 1;
+                bal &= bal - 1;
+                uint32_t Ts[WN];
+#pragma unroll
+                for (int w = 0; w < WN; w++) Ts[w] = __shfl_sync(FULL, T[w], s);
+                uint32_t js = i + 1 + jc * 32 + s;
+                idx[1] = js;
+                expand_narrow<3, R, WN>(m, Ts, idx, js + 1, l, acc, err);
+            }
+        }
+    }
+}
+
+// ---- wide anchors (more than 256 useful positions): masks streamed word by
+// word; warp-uniform prefixes live in a per-warp scratch (level L-1 at
+// pre + (L-2) * wmax).
+
+template <int R>
+__device__ __forceinline__ void leaf_wide(const Masks &m, const uint32_t *pre, uint32_t c,
+                                          const uint32_t (&idx)[R], int l, U128 &acc,
+                                          unsigned *err) {
+    // T = pre AND P(., c); pre == nullptr means T = P(., c)
+    if constexpr (R <= 3) {
+        uint32_t x[1 << R];
+#pragma unroll
+        for (int k = 0; k < (1 << R); k++) x[k] = 0;
+        for (uint32_t w = 0; w < m.W; w++) {
+            uint32_t t = m.P(w, c);
+            if (pre) t &= pre[w];
+            if (!t) continue;
+            uint32_t dd[R];
+#pragma unroll
+            for (int i = 0; i < R; i++) dd[i] = m.D(w, idx[i]);
+#pragma unroll
+            for (int k = 0; k < (1 << R); k++) {
+                uint32_t msk = t;
+#pragma unroll
+                for (int i = 0; i < R; i++) msk &= ((k >> i) & 1) ? dd[i] : ~dd[i];
+                x[k] += __popc(msk);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < (1 << R); k++) binom_add(acc, x[k], l, err);
+    } else {
+        uint32_t x[1 << R];
+        for (int k = 0; k < (1 << R); k++) x[k] = 0;
+        for (uint32_t w = 0; w < m.W; w++) {
+            uint32_t t = m.P(w, c);
+            if (pre) t &= pre[w];
+            while (t) {
+                int b = __ffs(t) - 1;
+                t &= t - 1;
+                uint32_t kk = 0;
+                for (int i = 0; i < R; i++) kk |= ((m.D(w, idx[i]) >> b) & 1u) << i;
+                x[kk]++;
+            }
+        }
+        for (int k = 0; k < (1 << R); k++) binom_add(acc, x[k], l, err);
+    }
+}
+
+template <int L, int R>
+__device__ void expand_wide(const Masks &m, uint32_t *scratch, uint32_t wmax,
+                            uint32_t (&idx)[R], uint32_t start, int l, U128 &acc, unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t *pre = scratch + (size_t)(L - 2) * wmax;  // prefix of L-1 partners
+    for (uint32_t mb = start; mb < m.nc; mb += 32) {
+        uint32_t c = mb + lane;
+        bool valid = c < m.nc;
+        uint32_t n = 0;
+        if (valid)
+            for (uint32_t w = 0; w < m.W; w++) n += __popc(pre[w] & m.P(w, c));
+        if constexpr (L == R) {
+            if (valid && (int)n >= l) {
+                uint32_t id2[R];
+#pragma unroll
+                for (int i = 0; i < R; i++) id2[i] = idx[i];
+                id2[R - 1] = c;
+                leaf_wide<R>(m, pre, c, id2, l, acc, err);
+            }
+        } else {
+            bool ok = valid && (int)n >= l && (m.nc - 1 - c) >= (uint32_t)(R - L);
+            uint32_t bal = __ballot_sync(FULL, ok);
+            while (bal) {
+                int s = __ffs(bal) - 1;
+                bal &= bal - 1;
+                uint32_t cs = mb + s;
+                uint32_t *nxt = scratch + (size_t)(L - 1) * wmax;
+                __syncwarp();
+                for (uint32_t w = lane; w < m.W; w += 32) nxt[w] = pre[w] & m.P(w, cs);
+                __syncwarp();
+                idx[L - 1] = cs;
+                expand_wide<L + 1, R>(m, scratch, wmax, idx, cs + 1, l, acc, err);
+            }
+        }
+    }
+}
+
+template <int R>
+__device__ void unit_wide(const Masks &m, uint32_t *scratch, uint32_t wmax, uint32_t i,
+                          uint32_t jc, int l, U128 &acc, unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    if constexpr (R == 1) {
+        uint32_t c = jc * 32 + lane;
+        if (c < m.nc) {
+            uint32_t n = 0;
+            for (uint32_t w = 0; w < m.W; w++) n += __popc(m.P(w, c));
+            if ((int)n >= l) {
+                uint32_t id[1] = {c};
+                leaf_wide<1>(m, nullptr, c, id, l, acc, err);
+            }
+        }
+    } else {
+        // level-1 prefix P(., i) at scratch[0 .. W)
+        __syncwarp();
+        for (uint32_t w = lane; w < m.W; w += 32) scratch[w] = m.P(w, i);
+        __syncwarp();
+        uint32_t j = i + 1 + jc * 32 + lane;
+        bool valid = j < m.nc;
+        uint32_t n = 0;
+        if (valid)
+            for (uint32_t w = 0; w < m.W; w++) n += __popc(scratch[w] & m.P(w, j));
+        if constexpr (R == 2) {
+            if (valid && (int)n >= l) {
+                uint32_t id[2] = {i, j};
+                leaf_wide<2>(m, scratch, j, id, l, acc, err);
+            }
+        } else {
+            bool ok = valid && (int)n >= l && (m.nc - 1 - j) >= (uint32_t)(R - 2);
+            uint32_t bal = __ballot_sync(FULL, ok);
+            uint32_t idx[R];
+            idx[0] = i;
+            while (bal) {
+                int s = __ffs(bal) - 1;
+                bal &= bal - 1;
+                uint32_t js = i + 1 + jc * 32 + s;
+                uint32_t *nxt = scratch + wmax;
+                __syncwarp();
+                for (uint32_t w = lane; w < m.W; w += 32) nxt[w] = scratch[w] & m.P(w, js);
+                __syncwarp();
+                idx[1] = js;
+                expand_wide<3, R>(m, scratch, wmax, idx, js + 1, l, acc, err);
+            }
+        }
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ int s_item;
+    __shared__ uint32_t s_unit, s_total;
+    __shared__ uint32_t s_rowpre[ROWS_MAX + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned *err = &a.cnt->err;
+    uint32_t *scratch =
+        a.wide_scratch ? a.wide_scratch + ((size_t)blockIdx.x * PB_WARPS + warp) * R * a.wmax : nullptr;
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(&a.cnt->head_b, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= (int)a.cnt->n_items) break;
+        const Item it = a.items[a.iorder[item]];
+        const uint32_t r = it.anchor;
+        const uint32_t nc = a.ncand[r];
+        const uint32_t W = (a.dprime[r] + 31) / 32;
+        const uint32_t rsv = a.rsv_c[r];
+        const uint32_t *region = a.pool + a.pool_off[r];
+        Masks m;
+        m.W = W;
+        m.nc = nc;
+        if (2ull * W * nc <= (unsigned long long)PB_SMEM_WORDS) {
+            for (uint32_t t = tid; t < 2 * W * nc; t += PB_THREADS) {
+                uint32_t wd = t / nc, c = t % nc;
+                sm[t] = region[(size_t)wd * rsv + c];
+            }
+            m.base = sm;
+            m.stride = nc;
+        } else {
+            m.base = region;
+            m.stride = rsv;
+        }
+        // unit layout
+        const bool split = it.u1 != 0;
+        if (tid == 0) {
+            s_unit = 0;
+            if (split) {
+                s_total = it.u1 - it.u0;
+            } else {
+                uint32_t acc = 0;
+                for (uint32_t i = it.i0; i < it.i1; i++) {
+                    s_rowpre[i - it.i0] = acc;
+                    acc += (nc - 1 - i + 31) / 32;
+                }
+                s_rowpre[it.i1 - it.i0] = acc;
+                s_total = acc;
+            }
+        }
+        __syncthreads();
+        const uint32_t total = s_total;
+        U128 acc;
+        for (;;) {
+            uint32_t u = 0;
+            if (lane == 0) u = atomicAdd(&s_unit, 1u);
+            u = __shfl_sync(FULL, u, 0);
+            if (u >= total) break;
+            uint32_t i, jc;
+            if (split) {
+                i = it.i0;
+                jc = it.u0 + u;
+            } else {
+                uint32_t lo = 0, hi = it.i1 - it.i0;  // largest k with rowpre[k] <= u
+                while (hi - lo > 1) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if (s_rowpre[mid] <= u) lo = mid; else hi = mid;
+                }
+                i = it.i0 + lo;
+                jc = u - s_rowpre[lo];
+            }
+            if (W <= 1) unit_narrow<R, 1>(m, i, jc, a.l, acc, err);
+            else if (W <= 2) unit_narrow<R, 2>(m, i, jc, a.l, acc, err);
+            else if (W <= 4) unit_narrow<R, 4>(m, i, jc, a.l, acc, err);
+            else if (W <= 8) unit_narrow<R, 8>(m, i, jc, a.l, acc, err);
+            else unit_wide<R>(m, scratch, a.wmax, i, jc, a.l, acc, err);
+        }
+        U128 ws = warp_sum_u128(acc);
+        if (lane == 0 && (ws.lo | ws.hi)) {
+            atomic_add_u128(a.cnt->total, ws.lo, ws.hi);
+            if (a.per_anchor) atomic_add_u128(a.per_anchor + 2 * (size_t)r, ws.lo, ws.hi);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+// Largest x with binom(x, l) computable in 64 bits by the multiplicative
+// formula: every partial product binom(x-l+i, i) * i must stay below 2^64.
+unsigned long long binom64_limit(int l) {
+    auto fits = [l](unsigned long long x) {
+        unsigned __int128 r = 1;
+        for (int i = 1; i <= l; i++) {
+            unsigned __int128 prod = r * (unsigned __int128)(x - l + i);
+            if (prod >> 64) return false;
+            r = prod / i;
+        }
+        return true;
+    };
+    unsigned long long lo = (unsigned long long)l, hi = 1ull << 40;
+    while (lo < hi) {
+        unsigned long long mid = lo + (hi - lo + 1) / 2;
+        if (fits(mid)) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int R>
+void set_tuple_attr() {
+    SBC_CUDA(cudaFuncSetAttribute(k_tuples<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)PB_SMEM));
+}
+
+// Opt every large-shared-memory kernel in once per process (per device).
+void ensure_kernel_attrs() {
+    static std::mutex mu;
+    static bool done = false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done) return;
+    SBC_CUDA(cudaFuncSetAttribute(k_twohop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PA_SMEM));
+    SBC_CUDA(cudaFuncSetAttribute(k_twohop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PA_SMEM));
+    set_tuple_attr<1>();
+    set_tuple_attr<2>();
+    set_tuple_attr<3>();
+    set_tuple_attr<4>();
+    set_tuple_attr<5>();
+    set_tuple_attr<6>();
+    set_tuple_attr<7>();
+    done = true;
+}
+
+template <int R>
+void launch_tuples(int grid, cudaStream_t s, const TupleArgs &a) {
+    k_tuples<R><<<grid, PB_THREADS, PB_SMEM, s>>>(a);
+    SBC_LAUNCHED();
+}
+
+int blocks_per_sm(const void *fn, int threads, size_t smem) {
+    int n = 0;
+    SBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem));
+    return n < 1 ? 1 : n;
+}
+
+struct EventTimer {
+    cudaEvent_t e[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool on;
+    explicit EventTimer(bool enable) : on(enable) {
+        if (on)
+            for (auto &x : e) SBC_CUDA(cudaEventCreate(&x));
+    }
+    void mark(int i, cudaStream_t s) {
+        if (on) SBC_CUDA(cudaEventRecord(e[i], s));
+    }
+    float ms(int a, int b) {
+        float t = 0;
+        if (on) SBC_CUDA(cudaEventElapsedTime(&t, e[a], e[b]));
+        return t;
+    }
+    ~EventTimer() {
+        for (auto &x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+}  // namespace
+
+void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
+                 sbc_count_stats *stats, cudaStream_t s) {
+    sbc_graph *g = const_cast<sbc_graph *>(gc);
+    if (p < 2 || q < 2 || p > 8 || q > 8) fail(SBC_E_INVAL, "p and q must be in [2, 8], got (%d, %d)", p, q);
+    int cur = 0;
+    SBC_CUDA(cudaGetDevice(&cur));
+    if (cur != g->device) fail(SBC_E_INVAL, "graph lives on device %d, current device is %d", g->device, cur);
+    int side = opts ? opts->anchor_side : SBC_SIDE_AUTO;
+    if (side == SBC_SIDE_AUTO) side = g->wedges_u <= g->wedges_v ? 0 : 1;
+    if (side != 0 && side != 1) fail(SBC_E_INVAL, "anchor_side must be -1, 0 or 1");
+    const int k = side == 0 ? p : q, l = side == 0 ? q : p, R = k - 1;
+    const bool paper = opts && (opts->flags & SBC_COUNT_PAPER_TUPLES);
+    const int shard = opts ? opts->shard : 0;
+    const int nshard = opts ? opts->shard_count : 0;
+    if (nshard < 0 || (nshard > 0 && (shard < 0 || shard >= nshard)))
+        fail(SBC_E_INVAL, "bad shard %d of %d", shard, nshard);
+    const int64_t kernels0 = g_launches;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->anchor_side = side;
+    }
+    const int64_t nX = side == 0 ? g->n_u : g->n_v;
+    if (opts && opts->per_anchor && nX > 0) memset(opts->per_anchor, 0, sizeof(sbc_u128) * (size_t)nX);
+    if (g->nnz == 0 || nX == 0) return;
+    ensure_kernel_attrs();
+    EventTimer tm(stats != nullptr);
+    tm.mark(0, s);
+    {
+        std::lock_guard<std::mutex> lock(g->mu);
+        build_orientation(g, side, s);
+    }
+    const Orient &o = g->side[side];
+    const int64_t nnz = g->nnz;
+    const int B = 256;
+
+    unsigned long long lim[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 2; i <= 8; i++) lim[i] = binom64_limit(i);
+    SBC_CUDA(cudaMemcpyToSymbolAsync(c_binom64_max, lim, sizeof(lim), 0, cudaMemcpyHostToDevice, s));
+
+    DevBuf<Counters> cnt(1, s);
+    SBC_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(Counters), s));
+    DevBuf<uint32_t> A_bit(nnz, s), dprime(nX, s), rsv_c(nX, s), skey(nX, s), sval(nX, s),
+        tk(nX, s), tv(nX, s), ncand(nX, s), npaper(paper ? nX : 0, s);
+    DevBuf<unsigned long long> e_use(nX, s), e_all(nX, s);
+    DevBuf<int64_t> pool_off(nX + 1, s), dtot(1, s);
+
+    k_plan<<<grid_for(nX * 32, B), B, 0, s>>>(o.A_off.ptr, o.A_ent.ptr, o.A_pos.ptr, o.B_off.ptr, nX,
+                                              R, l, shard, nshard, paper ? 1 : 0, A_bit.ptr,
+                                              dprime.ptr, e_use.ptr, e_all.ptr, rsv_c.ptr,
+                                              pool_off.ptr, skey.ptr, sval.ptr, cnt.ptr);
+    SBC_LAUNCHED();
+    g_launches++;
+    scan_exclusive_i64(pool_off.ptr, pool_off.ptr, nX + 1, dtot.ptr, s);
+    radix_sort_pairs(skey.ptr, sval.ptr, tk.ptr, tv.ptr, nX, 32, s);
+    SBC_CUDA(cudaMemsetAsync(ncand.ptr, 0, (size_t)nX * 4, s));
+    if (paper) SBC_CUDA(cudaMemsetAsync(npaper.ptr, 0, (size_t)nX * 4, s));
+    int64_t pool_words = 0;
+    Counters hc;
+    SBC_CUDA(cudaMemcpyAsync(&pool_words, dtot.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    SBC_CUDA(cudaStreamSynchronize(s));
+    DevBuf<uint32_t> pool((size_t)(pool_words > 0 ? pool_words : 1), s);
+    tm.mark(1, s);
+
+    const int sms = sm_count();
+    if (hc.n_active > 0) {
+        TwohopArgs ta;
+        ta.A_off = o.A_off.ptr;
+        ta.A_ent = o.A_ent.ptr;
+        ta.A_pos = o.A_pos.ptr;
+        ta.A_bit = A_bit.ptr;
+        ta.B_off = o.B_off.ptr;
+        ta.B_ent = o.B_ent.ptr;
+        ta.dprime = dprime.ptr;
+        ta.e_use = e_use.ptr;
+        ta.e_all = e_all.ptr;
+        ta.rsv_c = rsv_c.ptr;
+        ta.pool_off = pool_off.ptr;
+        ta.order = sval.ptr;
+        ta.pool = pool.ptr;
+        ta.ncand = ncand.ptr;
+        ta.npaper = paper ? npaper.ptr : nullptr;
+        ta.cnt = cnt.ptr;
+        ta.l = l;
+        const void *fn = paper ? (const void *)k_twohop<true> : (const void *)k_twohop<false>;
+        int ga = sms * blocks_per_sm(fn, PA_THREADS, PA_SMEM);
+        if ((int64_t)ga > (int64_t)hc.n_active) ga = (int)hc.n_active;
+        if (paper) k_twohop<true><<<ga, PA_THREADS, PA_SMEM, s>>>(ta);
+        else k_twohop<false><<<ga, PA_THREADS, PA_SMEM, s>>>(ta);
+        SBC_LAUNCHED();
+        g_launches++;
+    }
+    tm.mark(2, s);
+
+    // tuple phase planning
+    ItemArgs ia;
+    ia.ncand = ncand.ptr;
+    ia.npaper = paper ? npaper.ptr : nullptr;
+    ia.dprime = dprime.ptr;
+    ia.nX = nX;
+    ia.R = R;
+    ia.cnt = cnt.ptr;
+    ia.item_cost = 0;
+    ia.item_off = nullptr;
+    ia.item_cnt = nullptr;
+    ia.items = nullptr;
+    ia.ikey = ia.ival = nullptr;
+    k_anchor_cost<<<grid_for(nX, B), B, 0, s>>>(ia);
+    SBC_LAUNCHED();
+    g_launches++;
+    SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    SBC_CUDA(cudaStreamSynchronize(s));
+    const int gb = sms * blocks_per_sm((const void *)k_tuples<1>, PB_THREADS, PB_SMEM);
+    unsigned long long ic = hc.cost_total / ((unsigned long long)gb * PB_WARPS * 4ull);
+    if (ic < (1ull << 12)) ic = 1ull << 12;
+    if (ic > (1ull << 30)) ic = 1ull << 30;
+    ia.item_cost = ic;
+    DevBuf<int64_t> item_off(nX + 1, s);
+    ia.item_cnt = item_off.ptr;
+    int64_t n_items = 0;
+    if (hc.cost_total > 0 || R == 1) {
+        k_items<false><<<grid_for(nX, B), B, 0, s>>>(ia);
+        SBC_LAUNCHED();
+        scan_exclusive_i64(item_off.ptr, item_off.ptr, nX + 1, dtot.ptr, s);
+        g_launches++;
+        SBC_CUDA(cudaMemcpyAsync(&n_items, dtot.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SBC_CUDA(cudaStreamSynchronize(s));
+    }
+    if (n_items > 0xFFFFFFF0ll) fail(SBC_E_UNSUPPORTED, "too many work items");
+    if (n_items > 0) {
+        DevBuf<Item> items(n_items, s);
+        DevBuf<uint32_t> ikey(n_items, s), ival(n_items, s), t1(n_items, s), t2(n_items, s);
+        ia.item_off = item_off.ptr;
+        ia.items = items.ptr;
+        ia.ikey = ikey.ptr;
+        ia.ival = ival.ptr;
+        k_items<true><<<grid_for(nX, B), B, 0, s>>>(ia);
+        SBC_LAUNCHED();
+        g_launches++;
+        radix_sort_pairs(ikey.ptr, ival.ptr, t1.ptr, t2.ptr, n_items, 32, s);
+        unsigned ni = (unsigned)n_items;
+        SBC_CUDA(cudaMemcpyAsync(&cnt.ptr->n_items, &ni, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+        DevBuf<unsigned long long> per(opts && opts->per_anchor ? 2 * nX : 0, s);
+        if (per.ptr) SBC_CUDA(cudaMemsetAsync(per.ptr, 0, per.bytes(), s));
+        uint32_t wmax = (uint32_t)((o.max_deg_x + 31) / 32);
+        int grid = gb;
+        if ((int64_t)grid > n_items) grid = (int)n_items;
+        DevBuf<uint32_t> scratch(wmax > 8 ? (size_t)grid * PB_WARPS * R * wmax : 0, s);
+        TupleArgs tu;
+        tu.ncand = ncand.ptr;
+        tu.dprime = dprime.ptr;
+        tu.rsv_c = rsv_c.ptr;
+        tu.pool_off = pool_off.ptr;
+        tu.pool = pool.ptr;
+        tu.items = items.ptr;
+        tu.iorder = ival.ptr;
+        tu.cnt = cnt.ptr;
+        tu.per_anchor = per.ptr;
+        tu.wide_scratch = scratch.ptr;
+        tu.wmax = wmax;
+        tu.l = l;
+        tm.mark(3, s);
+        switch (R) {
+            case 1: launch_tuples<1>(grid, s, tu); break;
+            case 2: launch_tuples<2>(grid, s, tu); break;
+            case 3: launch_tuples<3>(grid, s, tu); break;
+            case 4: launch_tuples<4>(grid, s, tu); break;
+            case 5: launch_tuples<5>(grid, s, tu); break;
+            case 6: launch_tuples<6>(grid, s, tu); break;
+            default: launch_tuples<7>(grid, s, tu); break;
+        }
+        g_launches++;
+        tm.mark(4, s);
+        if (per.ptr) {
+            std::vector<unsigned long long> hp((size_t)2 * nX);
+            std::vector<int32_t> vo((size_t)nX);
+            SBC_CUDA(cudaMemcpyAsync(hp.data(), per.ptr, per.bytes(), cudaMemcpyDeviceToHost, s));
+            SBC_CUDA(cudaMemcpyAsync(vo.data(), o.vert_of.ptr, (size_t)nX * 4, cudaMemcpyDeviceToHost, s));
+            SBC_CUDA(cudaStreamSynchronize(s));
+            for (int64_t r = 0; r < nX; r++) {
+                opts->per_anchor[vo[r]].lo = hp[2 * r];
+                opts->per_anchor[vo[r]].hi = hp[2 * r + 1];
+            }
+        }
+    } else {
+        tm.mark(3, s);
+        tm.mark(4, s);
+    }
+    SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    SBC_CUDA(cudaStreamSynchronize(s));
+    if (hc.err & CERR_OVERFLOW) fail(SBC_E_OVERFLOW, "balanced biclique count exceeds 128 bits");
+    if (hc.err & (CERR_RESERVE | CERR_HASH))
+        fail(SBC_E_CUDA, "internal error in the 2-hop kernel (flags 0x%x)", hc.err);
+    if (stats) {
+        stats->count.lo = hc.total[0];
+        stats->count.hi = hc.total[1];
+        if (paper) {
+            stats->anchor_tuples.lo = hc.tuples_paper[0];
+            stats->anchor_tuples.hi = hc.tuples_paper[1];
+        } else {
+            stats->anchor_tuples.lo = hc.tuples_ours[0];
+            stats->anchor_tuples.hi = hc.tuples_ours[1];
+        }
+        stats->candidates = hc.candidates;
+        stats->wedges = hc.wedges;
+        stats->work_items = (uint64_t)n_items;
+        stats->kernels = (int32_t)(g_launches - kernels0);
+        stats->ms_prepare = tm.ms(0, 1) + tm.ms(2, 3);
+        stats->ms_twohop = tm.ms(1, 2);
+        stats->ms_tuples = tm.ms(3, 4);
+        stats->ms_total = tm.ms(0, 4);
+    }
+}
+
+}  // namespace sbc

@@ -1,0 +1,206 @@
+// Internal declarations shared by the CUDA sources of libsbc.
+//
+// Errors travel as C++ exceptions (SbcError) inside the library and are turned
+// into sbc_status codes plus a thread-local message at every C entry point.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <mutex>
+#include <memory>
+#include <stdexcept>
+#include <string>
+
+#include "../../include/sbc.h"
+
+namespace sbc {
+
+struct SbcError : std::runtime_error {
+    sbc_status status;
+    SbcError(sbc_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+[[noreturn]] void fail(sbc_status s, const char *fmt, ...);
+void set_last_error(const std::string &msg);
+
+#define SBC_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t err_ = (call);                                                       \
+        if (err_ != cudaSuccess)                                                         \
+            ::sbc::fail(err_ == cudaErrorMemoryAllocation ? SBC_E_NOMEM : SBC_E_CUDA,    \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(err_),        \
+                        __FILE__, __LINE__);                                             \
+    } while (0)
+
+// Check for a launch error right after a kernel launch.
+#define SBC_LAUNCHED() SBC_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- memory
+
+void *dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void *p, size_t bytes, cudaStream_t s);
+
+// Owning device buffer (stream-ordered allocation).
+template <typename T>
+struct DevBuf {
+    T *ptr = nullptr;
+    size_t n = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf() = default;
+    DevBuf(size_t count, cudaStream_t s) { alloc(count, s); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : ptr(o.ptr), n(o.n), stream(o.stream) { o.ptr = nullptr; o.n = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            ptr = o.ptr; n = o.n; stream = o.stream;
+            o.ptr = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    void alloc(size_t count, cudaStream_t s) {
+        release();
+        stream = s;
+        n = count;
+        ptr = count ? static_cast<T *>(dev_alloc(count * sizeof(T), s)) : nullptr;
+    }
+    void release() {
+        if (ptr) dev_free(ptr, n * sizeof(T), stream);
+        ptr = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+    ~DevBuf() { release(); }
+};
+
+// ---------------------------------------------------------------- graph
+
+// Structures for one anchor side X (Algorithm 2's S) of a graph. X-vertices
+// are renumbered by their rank in the vertex priority rho of Definition 4
+// (ascending degree, ties by ascending id), so "rho(w) > rho(u)" becomes
+// "rank(w) > rank(u)".
+struct Orient {
+    bool built = false;
+    int64_t nX = 0, nY = 0;
+    DevBuf<int64_t> A_off;   // nX+1: X->Y adjacency, rows in rank order
+    DevBuf<uint32_t> A_ent;  // nnz: y | (negative << 31)
+    DevBuf<uint32_t> A_pos;  // nnz: index of the mirror entry inside B's list of y
+    DevBuf<int64_t> B_off;   // nY+1: Y->X adjacency
+    DevBuf<uint32_t> B_ent;  // nnz: rank(x) | (negative << 31), each list ascending by rank
+    DevBuf<int32_t> vert_of; // nX: rank -> vertex id
+    int64_t max_deg_x = 0, max_deg_y = 0;
+    size_t bytes() const {
+        return A_off.bytes() + A_ent.bytes() + A_pos.bytes() + B_off.bytes() + B_ent.bytes() +
+               vert_of.bytes();
+    }
+};
+
+}  // namespace sbc
+
+struct sbc_graph {
+    int device = 0;
+    int64_t n_u = 0, n_v = 0, nnz = 0;
+    sbc::DevBuf<int64_t> off;  // n_u+1
+    sbc::DevBuf<int32_t> col;  // nnz
+    sbc::DevBuf<uint8_t> neg;  // nnz, 1 = negative edge
+    sbc::DevBuf<int32_t> deg_u, deg_v;
+    int64_t max_deg_u = 0, max_deg_v = 0;
+    uint64_t wedges_u = 0, wedges_v = 0;  // 2-paths visited anchoring on U / on V
+    sbc::Orient side[2];
+    std::mutex mu;
+    size_t bytes() const {
+        return off.bytes() + col.bytes() + neg.bytes() + deg_u.bytes() + deg_v.bytes() +
+               side[0].bytes() + side[1].bytes();
+    }
+};
+
+namespace sbc {
+
+// Build (once) the oriented structures of side `x` (0 = U, 1 = V).
+// Sets *dup when a duplicate (u, v) pair is found.
+void build_orientation(sbc_graph *g, int x, cudaStream_t s);
+
+// ---------------------------------------------------------------- primitives
+
+// Exclusive prefix sum of n values; in and out may alias. Returns nothing; the
+// total is out[n-1] + in[n-1] and can be requested with total != nullptr
+// (device pointer, one element).
+void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total,
+                        cudaStream_t s);
+void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
+                        cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of
+// the key. Sorted data ends in keys/vals; tmp_keys/tmp_vals are n-element
+// scratch buffers. `launches` is incremented by the kernels issued.
+void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys, uint32_t *tmp_vals,
+                      int64_t n, int key_bits, cudaStream_t s, int *launches = nullptr);
+
+// Number of bits needed to represent v (0 for v == 0).
+inline int bits_for(uint64_t v) {
+    int b = 0;
+    while (v) { b++; v >>= 1; }
+    return b;
+}
+
+inline int grid_for(int64_t n, int block, int cap = 152 * 32) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// Count of streaming multiprocessors of the current device.
+int sm_count();
+
+// Kernel launches issued by the library since load (for reporting).
+extern int64_t g_launches;
+
+// Count driver: defined in count.cu.
+void count_graph(const sbc_graph *g, int p, int q, const sbc_count_opts *opts,
+                 sbc_count_stats *stats, cudaStream_t s);
+
+}  // namespace sbc
+
+// ---------------------------------------------------------------- device helpers
+
+namespace sbc {
+
+// Add the unsigned 128-bit value (lo, hi) into *dst (two 64-bit words) with
+// 64-bit atomics: the limb add that wraps carries into the high word.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long *dst, unsigned long long lo,
+                                                unsigned long long hi) {
+    if (lo) {
+        unsigned long long old = atomicAdd(dst, lo);
+        if (old + lo < old) hi += 1;
+    }
+    if (hi) atomicAdd(dst + 1, hi);
+}
+
+struct U128 {
+    unsigned long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(unsigned long long v) {
+        lo += v;
+        hi += (lo < v) ? 1ull : 0ull;
+    }
+    __device__ __forceinline__ void add(U128 v) {
+        lo += v.lo;
+        hi += v.hi + ((lo < v.lo) ? 1ull : 0ull);
+    }
+};
+
+__device__ __forceinline__ U128 warp_sum_u128(U128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        U128 t;
+        t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        v.add(t);
+    }
+    return v;
+}
+
+}  // namespace sbc
