@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark: balanced (p,q)-biclique counting on one GB300 (or N, sharded).
+
+Workload (default): one seeded signed Chung-Lu graph, |U| = 200,000,
+|V| = 100,000, 2,000,000 edges (exponents 2.0 on U, 2.3 on V, two planted
+factions with about 75% positive edges, flip probability 0.15), counted for
+(p,q) = (3,3) and (4,4).
+
+A step is the whole hot path on device-resident CSR input: graph build
+(validation, degrees, vertex priority, oriented adjacency) + the (3,3) count +
+the (4,4) count. The metric is anchor tuples per second: the number of
+(k-1)-subsets of candidates Algorithm 2 enumerates (sum over anchors of
+binom(|C(u)|, k-1), counted exactly once, outside the timed region), over the
+step time. Between timed steps L2 is flushed by writing a 512 MiB buffer.
+
+--impl reference runs the CPU oracle (Algorithm 2 in plain C, all host cores)
+on a bounded random sample of anchors of the same workload and reports the
+same metric.
+
+Multi-GPU (torchrun): anchors are sharded by rank (anchor rank mod N) over a
+replicated graph; each rank counts its shard; partial counts are summed on the
+host. Total work is fixed, so scaling is strong.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "anchor tuples/sec and seconds to exact balanced (3,3) count; batched graphs/sec, p99"
+WORKLOAD = "plain-200k-100k-2M"
+PQ = [(3, 3), (4, 4)]
+POPC_PER_CLK_PER_SM = 16  # 32-bit population count throughput per SM per clock
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_workload():
+    import sbc_synth
+
+    return sbc_synth.plain_medium()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(g, p, q, frac, seed, threads=0):
+    """Oracle (Algorithm 2, C, OpenMP) on a seeded random anchor sample.
+    Returns (tuples, seconds, anchors, threads)."""
+    import oracle
+
+    side = 0  # the anchor side the cost model picks for this workload (U)
+    rng = np.random.default_rng(seed)
+    n_s = g.n_u if side == 0 else g.n_v
+    anchors = np.nonzero(rng.random(n_s) < frac)[0]
+    t0 = time.perf_counter()
+    _, tuples = oracle.count(g, p, q, side=side, threads=threads, with_tuples=True,
+                             anchors=anchors)
+    dt = time.perf_counter() - t0
+    return tuples, dt, len(anchors), oracle.max_threads() if threads == 0 else threads
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    g = load_workload()
+    frac = args.ref_frac
+    for i in range(args.warmup):
+        oracle_sample(g, 3, 3, frac, 100 + i)
+    tot_t, tot_tuples, cores, anchors = 0.0, 0, 0, 0
+    for i in range(args.steps):
+        tup, dt, na, cores = oracle_sample(g, 3, 3, frac, 1000 + i)
+        tot_t += dt
+        tot_tuples += tup
+        anchors += na
+    value = tot_tuples / tot_t
+    sample = (f"(3,3) on a seeded random {frac:.1%} sample of U anchors per step "
+              f"({anchors // max(args.steps, 1)} anchors), oracle = Algorithm 2 in C with OpenMP")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "anchor tuples/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * tot_t / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pq": "(3,3)", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "anchor tuples/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "anchor tuples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        gloo = dist.new_group(backend="gloo")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2605_03603_gb300 as sbc
+
+    dev = torch.cuda.current_device()
+    g = load_workload()
+    stream = torch.cuda.Stream()
+    off = torch.from_numpy(g.offsets).cuda()
+    col = torch.from_numpy(g.cols).cuda()
+    sgn = torch.from_numpy(g.signs).cuda()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    shard = dict(shard=rank, shard_count=ws) if ws > 1 else {}
+
+    # Algorithm 2's anchor tuples and the exact counts (untimed, once)
+    counts, tuples = {}, {}
+    with torch.cuda.stream(stream):
+        with sbc.sbc_graph_create(g.n_u, g.n_v, off, col, sgn, stream=stream) as h:
+            for p, q in PQ:
+                c, st, _ = sbc.sbc_count_ex(h, p, q, paper_tuples=True, stream=stream, **shard)
+                counts[(p, q)] = c
+                tuples[(p, q)] = st["anchor_tuples"]
+
+    def step():
+        with sbc.sbc_graph_create(g.n_u, g.n_v, off, col, sgn, stream=stream) as h:
+            out = []
+            for p, q in PQ:
+                c, st, _ = sbc.sbc_count_ex(h, p, q, stream=stream, **shard)
+                assert c == counts[(p, q)]
+                out.append(st)
+            return out
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ev33 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    per_step_stats = []
+    launches0 = sbc.sbc_launch_count()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush, outside the timed events
+            ev[i][0].record(stream)
+            ev33[i][0].record(stream)
+            with sbc.sbc_graph_create(g.n_u, g.n_v, off, col, sgn, stream=stream) as h:
+                sts = []
+                for j, (p, q) in enumerate(PQ):
+                    c, st, _ = sbc.sbc_count_ex(h, p, q, stream=stream, **shard)
+                    if j == 0:
+                        ev33[i][1].record(stream)
+                    sts.append(st)
+            ev[i][1].record(stream)
+            per_step_stats.append(sts)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = sbc.sbc_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms33 = [a.elapsed_time(b) for a, b in ev33]
+    ms = float(np.sum(step_ms))
+    if ws > 1:
+        allt = [None] * ws
+        dist.all_gather_object(allt, (ms, float(np.sum(ms33)), {str(k): v for k, v in counts.items()}), group=gloo)
+        ms = max(a[0] for a in allt)
+        ms33_tot = max(a[1] for a in allt)
+        totals = {}
+        for a in allt:
+            for k, v in a[2].items():
+                totals[k] = totals.get(k, 0) + v
+        tl = [None] * ws
+        dist.all_gather_object(tl, {str(k): v for k, v in tuples.items()}, group=gloo)
+        tuples_total = sum(sum(t.values()) for t in tl)
+    else:
+        ms33_tot = float(np.sum(ms33))
+        totals = {str(k): v for k, v in counts.items()}
+        tuples_total = sum(tuples.values())
+    ms_per_step = ms / args.steps
+    value = tuples_total / (ms_per_step / 1000.0)
+
+    # roofline of the dominant kernel (the tuple / type-count kernel)
+    peaks, peak_kind = measured_peaks()
+    tup_ms = [sum(s["ms_tuples"] for s in sts) for sts in per_step_stats]
+    hop_ms = [sum(s["ms_twohop"] for s in sts) for sts in per_step_stats]
+    popc = sum(s["popc_words"] for s in per_step_stats[0])
+    nlaunch = len(PQ)
+    avg_launch_ms = float(np.mean(tup_ms)) / nlaunch
+    achieved = (popc / nlaunch) / (avg_launch_ms / 1000.0) / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak = sm_count * POPC_PER_CLK_PER_SM * clk * 1e6 / 1e12
+    roof = {"kernel": "k_tuples (tuple enumeration, AND/POPC type counts)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak,
+            "traffic": None,
+            "peak_basis": f"{sm_count} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {clk:.0f} MHz "
+                          f"(median SM clock sampled under load)",
+            "share_of_step": float(np.mean(tup_ms) / np.mean(step_ms))}
+
+    # end to end through the public API with pinned host buffers
+    h_off = torch.from_numpy(g.offsets).pin_memory()
+    h_col = torch.from_numpy(g.cols).pin_memory()
+    h_sgn = torch.from_numpy(g.signs).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(e2e_steps)]
+    with torch.cuda.stream(stream):
+        for i in range(e2e_steps):
+            flush.zero_()
+            e2e_ev[i][0].record(stream)
+            with sbc.sbc_graph_create(g.n_u, g.n_v, h_off, h_col, h_sgn, stream=stream) as h:
+                for p, q in PQ:
+                    assert sbc.sbc_count(h, p, q, stream=stream) == counts[(p, q)]
+            e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in e2e_ev]))
+    if ws > 1:
+        allt = [None] * ws
+        dist.all_gather_object(allt, e2e_ms, group=gloo)
+        e2e_ms = max(allt)
+    h2d = g.offsets.nbytes + g.cols.nbytes + g.signs.nbytes
+    e2e = {"value": tuples_total / (e2e_ms / 1000.0), "unit": "anchor tuples/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 * len(PQ),
+           "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        tup, dt, na, cores = oracle_sample(g, 3, 3, args.cpu_frac, 7)
+        cpu = {"value": tup / dt, "unit": "anchor tuples/s", "cores": cores, "kind": "oracle",
+               "sample": f"(3,3) on a seeded random {args.cpu_frac:.1%} sample of U anchors "
+                         f"({na} anchors, {tup} tuples, {dt:.1f} s)"}
+
+    if rank == 0:
+        s0 = per_step_stats[0]
+        line = {
+            "metric": METRIC, "value": value, "unit": "anchor tuples/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "u32/u64 integer (exact u128 counts)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pq": "(3,3)+(4,4)", "n_u": g.n_u, "n_v": g.n_v,
+                       "edges": g.m, "seed": 2, "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": f"anchor shards x{ws}" if ws > 1 else "1 GPU"},
+            "seconds_to_exact_33": ms33_tot / args.steps / 1000.0,
+            "counts": totals, "anchor_tuples": {str(k): v for k, v in tuples.items()},
+            "phase_ms": {"tuples": float(np.mean(tup_ms)), "twohop": float(np.mean(hop_ms)),
+                         "other": float(np.mean(step_ms) - np.mean(tup_ms) - np.mean(hop_ms))},
+            "tuples_tested": [s["tuples_tested"] for s in s0],
+            "tuples_typed": [s["tuples_typed"] for s in s0],
+            "roofline": roof, "peak_source": peak_kind,
+            "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frac", type=float, default=0.10,
+                    help="anchor sample fraction for the oracle CPU baseline")
+    ap.add_argument("--ref-frac", type=float, default=0.02,
+                    help="anchor sample fraction per step for --impl reference")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

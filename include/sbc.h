@@ -140,6 +140,11 @@ typedef struct {
     uint64_t candidates;    /* sum over anchors of |C(u)| */
     uint64_t wedges;        /* 2-hop entries visited */
     uint64_t work_items;    /* tuple-phase work items launched */
+    uint64_t tuples_tested; /* tuples whose common-neighbour mask was tested (after
+                               nested pruning) */
+    uint64_t tuples_typed;  /* tuples with at least q common neighbours (type counts taken) */
+    uint64_t popc_words;    /* mask words popcounted by the tuple kernel: one per word of
+                               every tested tuple, 2^(k-1) per word of every typed tuple */
     int32_t anchor_side;    /* side used */
     int32_t kernels;        /* kernel launches issued by the call */
     float ms_prepare;       /* orientation build (first use of a side) + plan */
@@ -174,6 +179,10 @@ const char *sbc_last_error(void);
 
 /* Library version string. */
 const char *sbc_version(void);
+
+/* Kernel launches issued by the library in this process so far (all
+ * threads); the difference around a call counts its launches. */
+uint64_t sbc_launch_count(void);
 
 /*
  * Route the library's device allocations through caller functions (for

@@ -20,6 +20,7 @@ from . import build as _build
 __all__ = [
     "SbcError", "Graph", "sbc_graph_create", "sbc_graph_destroy", "sbc_graph_info",
     "sbc_count", "sbc_count_ex", "sbc_count_csr", "sbc_last_error", "sbc_version",
+    "sbc_launch_count",
     "lib", "LIB_PATH",
 ]
 
@@ -66,6 +67,8 @@ class CountOpts(ctypes.Structure):
 class CountStats(ctypes.Structure):
     _fields_ = [("count", U128), ("anchor_tuples", U128), ("candidates", ctypes.c_uint64),
                 ("wedges", ctypes.c_uint64), ("work_items", ctypes.c_uint64),
+                ("tuples_tested", ctypes.c_uint64), ("tuples_typed", ctypes.c_uint64),
+                ("popc_words", ctypes.c_uint64),
                 ("anchor_side", ctypes.c_int32), ("kernels", ctypes.c_int32),
                 ("ms_prepare", ctypes.c_float), ("ms_twohop", ctypes.c_float),
                 ("ms_tuples", ctypes.c_float), ("ms_total", ctypes.c_float)]
@@ -73,7 +76,9 @@ class CountStats(ctypes.Structure):
     def as_dict(self) -> dict:
         return {"count": self.count.value(), "anchor_tuples": self.anchor_tuples.value(),
                 "candidates": int(self.candidates), "wedges": int(self.wedges),
-                "work_items": int(self.work_items), "anchor_side": int(self.anchor_side),
+                "work_items": int(self.work_items), "tuples_tested": int(self.tuples_tested),
+                "tuples_typed": int(self.tuples_typed), "popc_words": int(self.popc_words),
+                "anchor_side": int(self.anchor_side),
                 "kernels": int(self.kernels), "ms_prepare": float(self.ms_prepare),
                 "ms_twohop": float(self.ms_twohop), "ms_tuples": float(self.ms_tuples),
                 "ms_total": float(self.ms_total)}
@@ -102,6 +107,12 @@ _declare("sbc_count_csr", ctypes.c_int,
           ctypes.POINTER(U128), _vp])
 _declare("sbc_last_error", ctypes.c_char_p, [])
 _declare("sbc_version", ctypes.c_char_p, [])
+_declare("sbc_launch_count", ctypes.c_uint64, [])
+
+
+def sbc_launch_count() -> int:
+    """Kernel launches issued by the library so far in this process."""
+    return int(lib.sbc_launch_count())
 
 
 class SbcError(RuntimeError):

@@ -7,7 +7,7 @@
 
 namespace sbc {
 
-int64_t g_launches = 0;
+std::atomic<int64_t> g_launches{0};
 
 namespace {
 thread_local std::string t_err;
@@ -87,6 +87,8 @@ extern "C" {
 const char *sbc_last_error(void) { return t_err.c_str(); }
 
 const char *sbc_version(void) { return "sbc 0.1 (sm_103a)"; }
+
+uint64_t sbc_launch_count(void) { return (uint64_t)g_launches.load(); }
 
 sbc_status sbc_set_allocator(sbc_alloc_fn alloc, sbc_free_fn free, void *ctx) {
     SBC_API_BEGIN

@@ -48,6 +48,9 @@ struct Counters {
     unsigned long long candidates;     // sum |C'| (or |C_paper| in stats mode)
     unsigned long long wedges;         // 2-hop entries visited
     unsigned long long cost_total;     // tuple-phase cost estimate
+    unsigned long long tested;         // tuples whose common-neighbour mask was tested
+    unsigned long long leaves;         // tuples with |T| >= l (type counts taken)
+    unsigned long long popc_words;     // mask words popcounted: W per test, 2^R W per leaf
     unsigned int n_active;             // anchors with work
     unsigned int head_a;               // 2-hop queue head
     unsigned int head_b;               // tuple queue head
@@ -654,6 +657,14 @@ struct TupleArgs {
     int l;
 };
 
+// Per-lane work tally of the tuple kernel (the algorithmic operations: one
+// AND+POPC per mask word of every tested tuple, 2^R masked POPCs per word of
+// every tuple that reaches the type count).
+struct Acc {
+    U128 sum;
+    unsigned long long tested = 0, leaves = 0, words = 0;
+};
+
 // View of an anchor's candidate masks: P(w, c) and D(w, c).
 struct Masks {
     const uint32_t *base;
@@ -670,8 +681,10 @@ struct Masks {
 // neighbourhood mask; idx[0..R-1]: the tuple's candidate indices.
 template <int R, int WN>
 __device__ __forceinline__ void leaf_narrow(const Masks &m, const uint32_t (&T)[WN],
-                                            const uint32_t (&idx)[R], int l, U128 &acc,
+                                            const uint32_t (&idx)[R], int l, Acc &acc,
                                             unsigned *err) {
+    acc.leaves++;
+    acc.words += (unsigned long long)m.W << R;
     if constexpr (R <= 3) {
         uint32_t x[1 << R];
 #pragma unroll
@@ -691,7 +704,7 @@ __device__ __forceinline__ void leaf_narrow(const Masks &m, const uint32_t (&T)[
             }
         }
 #pragma unroll
-        for (int k = 0; k < (1 << R); k++) binom_add(acc, x[k], l, err);
+        for (int k = 0; k < (1 << R); k++) binom_add(acc.sum, x[k], l, err);
     } else {
         // split T by each partner's type letter, dropping parts below l
         uint32_t stk[R + 1][WN];
@@ -711,7 +724,7 @@ __device__ __forceinline__ void leaf_narrow(const Masks &m, const uint32_t (&T)[
                 uint32_t n = 0;
 #pragma unroll
                 for (int w = 0; w < WN; w++) n += __popc(cur[w]);
-                binom_add(acc, n, l, err);
+                binom_add(acc.sum, n, l, err);
                 continue;
             }
             uint32_t a0[WN], a1[WN];
@@ -744,7 +757,7 @@ __device__ __forceinline__ void leaf_narrow(const Masks &m, const uint32_t (&T)[
 // candidate m >= start, lanes over m.
 template <int L, int R, int WN>
 __device__ void expand_narrow(const Masks &m, const uint32_t (&pre)[WN], uint32_t (&idx)[R],
-                              uint32_t start, int l, U128 &acc, unsigned *err) {
+                              uint32_t start, int l, Acc &acc, unsigned *err) {
     const int lane = threadIdx.x & 31;
     for (uint32_t mb = start; mb < m.nc; mb += 32) {
         uint32_t c = mb + lane;
@@ -755,6 +768,10 @@ __device__ void expand_narrow(const Masks &m, const uint32_t (&pre)[WN], uint32_
         for (int w = 0; w < WN; w++) {
             T[w] = (valid && w < (int)m.W) ? (pre[w] & m.P(w, c)) : 0u;
             n += __popc(T[w]);
+        }
+        if (valid) {
+            acc.tested++;
+            acc.words += m.W;
         }
         if constexpr (L == R) {
             if (valid && (int)n >= l) {
@@ -783,12 +800,14 @@ __device__ void expand_narrow(const Masks &m, const uint32_t (&pre)[WN], uint32_
 // One work unit: row i (first partner) and a chunk of 32 second partners;
 // for R == 1 a chunk of 32 single partners.
 template <int R, int WN>
-__device__ void unit_narrow(const Masks &m, uint32_t i, uint32_t jc, int l, U128 &acc,
+__device__ void unit_narrow(const Masks &m, uint32_t i, uint32_t jc, int l, Acc &acc,
                             unsigned *err) {
     const int lane = threadIdx.x & 31;
     if constexpr (R == 1) {
         uint32_t c = jc * 32 + lane;
         if (c < m.nc) {
+            acc.tested++;
+            acc.words += m.W;
             uint32_t T[WN];
             uint32_t n = 0;
 #pragma unroll
@@ -813,6 +832,10 @@ __device__ void unit_narrow(const Masks &m, uint32_t i, uint32_t jc, int l, U128
         for (int w = 0; w < WN; w++) {
             T[w] = valid ? (Pi[w] & ((w < (int)m.W) ? m.P(w, j) : 0u)) : 0u;
             n += __popc(T[w]);
+        }
+        if (valid) {
+            acc.tested++;
+            acc.words += m.W;
         }
         if constexpr (R == 2) {
             if (valid && (int)n >= l) {
@@ -844,8 +867,10 @@ __device__ void unit_narrow(const Masks &m, uint32_t i, uint32_t jc, int l, U128
 
 template <int R>
 __device__ __forceinline__ void leaf_wide(const Masks &m, const uint32_t *pre, uint32_t c,
-                                          const uint32_t (&idx)[R], int l, U128 &acc,
+                                          const uint32_t (&idx)[R], int l, Acc &acc,
                                           unsigned *err) {
+    acc.leaves++;
+    acc.words += (unsigned long long)m.W << R;
     // T = pre AND P(., c); pre == nullptr means T = P(., c)
     if constexpr (R <= 3) {
         uint32_t x[1 << R];
@@ -867,7 +892,7 @@ __device__ __forceinline__ void leaf_wide(const Masks &m, const uint32_t *pre, u
             }
         }
 #pragma unroll
-        for (int k = 0; k < (1 << R); k++) binom_add(acc, x[k], l, err);
+        for (int k = 0; k < (1 << R); k++) binom_add(acc.sum, x[k], l, err);
     } else {
         uint32_t x[1 << R];
         for (int k = 0; k < (1 << R); k++) x[k] = 0;
@@ -882,21 +907,24 @@ __device__ __forceinline__ void leaf_wide(const Masks &m, const uint32_t *pre, u
                 x[kk]++;
             }
         }
-        for (int k = 0; k < (1 << R); k++) binom_add(acc, x[k], l, err);
+        for (int k = 0; k < (1 << R); k++) binom_add(acc.sum, x[k], l, err);
     }
 }
 
 template <int L, int R>
 __device__ void expand_wide(const Masks &m, uint32_t *scratch, uint32_t wmax,
-                            uint32_t (&idx)[R], uint32_t start, int l, U128 &acc, unsigned *err) {
+                            uint32_t (&idx)[R], uint32_t start, int l, Acc &acc, unsigned *err) {
     const int lane = threadIdx.x & 31;
     const uint32_t *pre = scratch + (size_t)(L - 2) * wmax;  // prefix of L-1 partners
     for (uint32_t mb = start; mb < m.nc; mb += 32) {
         uint32_t c = mb + lane;
         bool valid = c < m.nc;
         uint32_t n = 0;
-        if (valid)
+        if (valid) {
+            acc.tested++;
+            acc.words += m.W;
             for (uint32_t w = 0; w < m.W; w++) n += __popc(pre[w] & m.P(w, c));
+        }
         if constexpr (L == R) {
             if (valid && (int)n >= l) {
                 uint32_t id2[R];
@@ -925,11 +953,13 @@ __device__ void expand_wide(const Masks &m, uint32_t *scratch, uint32_t wmax,
 
 template <int R>
 __device__ void unit_wide(const Masks &m, uint32_t *scratch, uint32_t wmax, uint32_t i,
-                          uint32_t jc, int l, U128 &acc, unsigned *err) {
+                          uint32_t jc, int l, Acc &acc, unsigned *err) {
     const int lane = threadIdx.x & 31;
     if constexpr (R == 1) {
         uint32_t c = jc * 32 + lane;
         if (c < m.nc) {
+            acc.tested++;
+            acc.words += m.W;
             uint32_t n = 0;
             for (uint32_t w = 0; w < m.W; w++) n += __popc(m.P(w, c));
             if ((int)n >= l) {
@@ -945,8 +975,11 @@ __device__ void unit_wide(const Masks &m, uint32_t *scratch, uint32_t wmax, uint
         uint32_t j = i + 1 + jc * 32 + lane;
         bool valid = j < m.nc;
         uint32_t n = 0;
-        if (valid)
+        if (valid) {
+            acc.tested++;
+            acc.words += m.W;
             for (uint32_t w = 0; w < m.W; w++) n += __popc(scratch[w] & m.P(w, j));
+        }
         if constexpr (R == 2) {
             if (valid && (int)n >= l) {
                 uint32_t id[2] = {i, j};
@@ -1025,7 +1058,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
         }
         __syncthreads();
         const uint32_t total = s_total;
-        U128 acc;
+        Acc acc;
         for (;;) {
             uint32_t u = 0;
             if (lane == 0) u = atomicAdd(&s_unit, 1u);
@@ -1050,10 +1083,21 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
             else if (W <= 8) unit_narrow<R, 8>(m, i, jc, a.l, acc, err);
             else unit_wide<R>(m, scratch, a.wmax, i, jc, a.l, acc, err);
         }
-        U128 ws = warp_sum_u128(acc);
+        U128 ws = warp_sum_u128(acc.sum);
         if (lane == 0 && (ws.lo | ws.hi)) {
             atomic_add_u128(a.cnt->total, ws.lo, ws.hi);
             if (a.per_anchor) atomic_add_u128(a.per_anchor + 2 * (size_t)r, ws.lo, ws.hi);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.tested += __shfl_xor_sync(FULL, acc.tested, o);
+            acc.leaves += __shfl_xor_sync(FULL, acc.leaves, o);
+            acc.words += __shfl_xor_sync(FULL, acc.words, o);
+        }
+        if (lane == 0 && acc.tested) {
+            atomicAdd(&a.cnt->tested, acc.tested);
+            atomicAdd(&a.cnt->leaves, acc.leaves);
+            atomicAdd(&a.cnt->popc_words, acc.words);
         }
         __syncthreads();
     }
@@ -1160,7 +1204,7 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     const int nshard = opts ? opts->shard_count : 0;
     if (nshard < 0 || (nshard > 0 && (shard < 0 || shard >= nshard)))
         fail(SBC_E_INVAL, "bad shard %d of %d", shard, nshard);
-    const int64_t kernels0 = g_launches;
+    const int64_t kernels0 = g_launches.load();
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->anchor_side = side;
@@ -1350,7 +1394,10 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
         stats->candidates = hc.candidates;
         stats->wedges = hc.wedges;
         stats->work_items = (uint64_t)n_items;
-        stats->kernels = (int32_t)(g_launches - kernels0);
+        stats->tuples_tested = hc.tested;
+        stats->tuples_typed = hc.leaves;
+        stats->popc_words = hc.popc_words;
+        stats->kernels = (int32_t)(g_launches.load() - kernels0);
         stats->ms_prepare = tm.ms(0, 1) + tm.ms(2, 3);
         stats->ms_twohop = tm.ms(1, 2);
         stats->ms_tuples = tm.ms(3, 4);

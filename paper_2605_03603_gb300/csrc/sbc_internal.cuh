@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <atomic>
 #include <mutex>
 #include <memory>
 #include <stdexcept>
@@ -157,7 +158,7 @@ inline int grid_for(int64_t n, int block, int cap = 152 * 32) {
 int sm_count();
 
 // Kernel launches issued by the library since load (for reporting).
-extern int64_t g_launches;
+extern std::atomic<int64_t> g_launches;
 
 // Count driver: defined in count.cu.
 void count_graph(const sbc_graph *g, int p, int q, const sbc_count_opts *opts,
