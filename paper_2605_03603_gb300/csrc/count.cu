@@ -52,7 +52,9 @@ struct Counters {
     unsigned long long leaves;         // tuples with |T| >= l (type counts taken)
     unsigned long long popc_words;     // mask words popcounted: W per test, 2^R W per leaf
     unsigned int n_active;             // anchors with work
-    unsigned int head_a;               // 2-hop queue head
+    unsigned int n_big;                // anchors for the CTA-wide 2-hop kernel
+    unsigned int head_large;           // 2-hop queue heads
+    unsigned int head_small;
     unsigned int head_b;               // tuple queue head
     unsigned int n_items;
     unsigned int err;                  // error bits
@@ -164,7 +166,7 @@ __global__ void k_plan(const int64_t *__restrict__ A_off, const uint32_t *__rest
                        unsigned long long *__restrict__ e_use, unsigned long long *__restrict__ e_all,
                        uint32_t *__restrict__ rsv_c, int64_t *__restrict__ rsv_w,
                        uint32_t *__restrict__ skey, uint32_t *__restrict__ sval,
-                       Counters *cnt) {
+                       Counters *cnt, int small_e) {
     const int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -216,6 +218,7 @@ __global__ void k_plan(const int64_t *__restrict__ A_off, const uint32_t *__rest
                              : 0xFFFFFFFFu;
             sval[r] = (uint32_t)r;
             if (active) atomicAdd(&cnt->n_active, 1u);
+            if (active && cost > (unsigned long long)small_e) atomicAdd(&cnt->n_big, 1u);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) rsv_w[nX] = 0;
@@ -223,39 +226,114 @@ __global__ void k_plan(const int64_t *__restrict__ A_off, const uint32_t *__rest
 
 // ------------------------------------------------------------------ 2-hop
 
-constexpr int PA_THREADS = 256;
-constexpr int PA_HS_MAX = 4096;            // hash slots
-constexpr int PA_WCAP = PA_HS_MAX / 2;     // wedges per window (load factor <= 1/2)
-constexpr int PA_STAGE_WORDS = 8192;       // staged P/D words
-constexpr size_t PA_SMEM = PA_HS_MAX * 4 + PA_HS_MAX * 8 + PA_STAGE_WORDS * 4;
+// Hash value: three 21-bit counters of one 2-hop partner w of the anchor.
+//   bits  0..20  cnt over all positions (Algorithm 2's cnt[w])
+//   bits 21..41  cnt over useful positions (|P_w|)
+//   bits 42..62  useful positions with sign(u,v) != sign(w,v) (|D_w|)
+//   bit  63      set once w is kept; the low 32 bits then hold its index
+constexpr unsigned long long F_ALL = 1ull, F_USE = 1ull << 21, F_DIFF = 1ull << 42;
+constexpr unsigned long long M21 = (1ull << 21) - 1;
+constexpr unsigned long long CAND = 1ull << 63;
+constexpr uint32_t NOBIT = 0x7FFFFFFFu;
 
-__device__ __forceinline__ uint32_t slot_of(uint32_t w, int lg) {
-    return (w * 0x9E3779B1u) >> (32 - lg);
+__device__ __forceinline__ uint32_t hash_slot(uint32_t w, uint32_t hs) {
+    return __umulhi(w * 0x9E3779B1u, hs);
 }
 __device__ __forceinline__ uint32_t class_of(uint32_t w, int lg) {
-    return lg ? ((w * 0x85EBCA6Bu) ^ (w >> 15)) * 0xC2B2AE35u >> (32 - lg) : 0u;
+    return lg ? (((w * 0x85EBCA6Bu) ^ (w >> 15)) * 0xC2B2AE35u) >> (32 - lg) : 0u;
 }
 
-// Visit every 2-hop entry of the anchor: all positions (stats pass) or only
-// the useful ones. fn(w, sdiff, bit, useful) runs for entries whose hash class
-// equals `cls` (lg_nw = log2 of the class count).
+// Add `add` to w's counters (open addressing, linear probing, at most hs
+// probes). Returns false when the table is full.
+__device__ __forceinline__ bool tab_insert(uint32_t *keys, unsigned long long *vals, uint32_t hs,
+                                           uint32_t w, unsigned long long add) {
+    uint32_t sl = hash_slot(w, hs);
+    for (uint32_t probes = 0; probes < hs; probes++) {
+        uint32_t k = keys[sl];
+        if (k == EMPTY) {
+            uint32_t old = atomicCAS(&keys[sl], EMPTY, w);
+            if (old == EMPTY || old == w) {
+                atomicAdd(&vals[sl], add);
+                return true;
+            }
+            k = old;
+        }
+        if (k == w) {
+            atomicAdd(&vals[sl], add);
+            return true;
+        }
+        sl = (sl + 1 == hs) ? 0u : sl + 1;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int tab_find(const uint32_t *keys, uint32_t hs, uint32_t w) {
+    uint32_t sl = hash_slot(w, hs);
+    for (uint32_t probes = 0; probes < hs; probes++) {
+        uint32_t k = keys[sl];
+        if (k == w) return (int)sl;
+        if (k == EMPTY) return -1;
+        sl = (sl + 1 == hs) ? 0u : sl + 1;
+    }
+    return -1;
+}
+
+// Candidate filter. Algorithm 2 keeps w when cnt[w] >= l. Every type class
+// of a tuple through w lies inside the same-sign or the different-sign part
+// of L[w] (the letter c_w is constant on a class), so only w with one part of
+// at least l useful common neighbours can add a non-zero binomial; the others
+// are dropped here, which changes no term of the sum.
+__device__ __forceinline__ bool keep_candidate(unsigned long long v, int l) {
+    uint32_t use = (uint32_t)((v >> 21) & M21), diff = (uint32_t)((v >> 42) & M21);
+    return use - diff >= (uint32_t)l || diff >= (uint32_t)l;
+}
+
+__device__ __forceinline__ unsigned long long pass1_add(uint32_t sdiff, uint32_t bit) {
+    return bit != EMPTY ? (F_ALL | F_USE | (sdiff ? F_DIFF : 0ull)) : F_ALL;
+}
+
+struct TwohopArgs {
+    const int64_t *A_off;
+    const uint32_t *A_ent, *A_pos, *A_bit;
+    const int64_t *B_off;
+    const uint32_t *B_ent;
+    const uint32_t *dprime;
+    const unsigned long long *e_use, *e_all;
+    const uint32_t *rsv_c;
+    const int64_t *pool_off;
+    const uint32_t *order;
+    uint32_t *pool;
+    uint32_t *ncand, *npaper;
+    Counters *cnt;
+    int l;
+};
+
+// ---- small anchors: one warp per anchor, private table in shared memory
+
+constexpr int PS_THREADS = 256;
+constexpr int PS_WARPS = PS_THREADS / 32;
+constexpr int PS_HS = 1024;            // slots per warp
+constexpr int SMALL_E = PS_HS / 2;     // visited wedges of a small anchor (load <= 1/2)
+constexpr size_t PS_SMEM = (size_t)PS_WARPS * PS_HS * 12;
+
+// Visit the anchor's 2-hop entries with one warp. fn(w, sdiff, bit).
 template <typename F>
-__device__ __forceinline__ void visit_twohop(int64_t ebase, int d, bool useful_only, int lg_nw,
-                                             uint32_t cls, const uint32_t *__restrict__ A_ent,
-                                             const uint32_t *__restrict__ A_pos,
-                                             const uint32_t *__restrict__ A_bit,
-                                             const int64_t *__restrict__ B_off,
-                                             const uint32_t *__restrict__ B_ent, F fn) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int g = warp * 32; g < d; g += nw * 32) {
+__device__ __forceinline__ void visit_warp(int64_t ebase, int d, bool useful_only,
+                                           const uint32_t *__restrict__ A_ent,
+                                           const uint32_t *__restrict__ A_pos,
+                                           const uint32_t *__restrict__ A_bit,
+                                           const int64_t *__restrict__ B_off,
+                                           const uint32_t *__restrict__ B_ent, F fn) {
+    const int lane = threadIdx.x & 31;
+    for (int g = 0; g < d; g += 32) {
         int j = g + lane;
         int64_t start = 0;
         uint32_t len = 0, su = 0, bit = EMPTY;
         if (j < d) {
             int64_t e = ebase + j;
-            uint32_t a = A_ent[e];
-            uint32_t y = a & VMASK;
-            su = a >> 31;
+            uint32_t av = A_ent[e];
+            uint32_t y = av & VMASK;
+            su = av >> 31;
             bit = A_bit[e];
             start = B_off[y] + (int64_t)A_pos[e] + 1;
             len = (uint32_t)(B_off[y + 1] - start);
@@ -283,45 +361,209 @@ __device__ __forceinline__ void visit_twohop(int64_t ebase, int d, bool useful_o
             uint32_t bits = __shfl_sync(FULL, bit, s);
             if (idx < total) {
                 uint32_t ent = B_ent[st + (idx - exs)];
-                uint32_t w = ent & VMASK;
-                if (class_of(w, lg_nw) == cls) fn(w, sus ^ (ent >> 31), bits);
+                fn(ent & VMASK, sus ^ (ent >> 31), bits);
             }
         }
     }
 }
 
-struct TwohopArgs {
-    const int64_t *A_off;
-    const uint32_t *A_ent, *A_pos, *A_bit;
-    const int64_t *B_off;
-    const uint32_t *B_ent;
-    const uint32_t *dprime;
-    const unsigned long long *e_use, *e_all;
-    const uint32_t *rsv_c;
-    const int64_t *pool_off;
-    const uint32_t *order;
-    uint32_t *pool;
-    uint32_t *ncand, *npaper;
-    Counters *cnt;
-    int l;
-};
-
 template <bool STATS>
-__global__ void __launch_bounds__(PA_THREADS) k_twohop(TwohopArgs a) {
+__global__ void __launch_bounds__(PS_THREADS) k_twohop_small(TwohopArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t *keys = (uint32_t *)smem_raw;
-    unsigned long long *vals = (unsigned long long *)(smem_raw + PA_HS_MAX * 4);
-    uint32_t *stage = (uint32_t *)(smem_raw + PA_HS_MAX * 12);
-    __shared__ int s_item;
-    __shared__ unsigned s_ncw, s_paper, s_ovf;
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *keys = (uint32_t *)(smem_raw + (size_t)warp * PS_HS * 4);
+    unsigned long long *vals =
+        (unsigned long long *)(smem_raw + (size_t)PS_WARPS * PS_HS * 4 + (size_t)warp * PS_HS * 8);
     const int l = a.l;
+    const uint32_t lt = (1u << lane) - 1u;
+    const unsigned n_big = a.cnt->n_big, n_act = a.cnt->n_active;
     unsigned long long wedges = 0;
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(&a.cnt->head_a, 1u);
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(&a.cnt->head_small, 1u);
+        item = __shfl_sync(FULL, item, 0) + n_big;
+        if (item >= n_act) break;
+        const uint32_t r = a.order[item];
+        const int64_t ebase = a.A_off[r];
+        const int d = (int)(a.A_off[r + 1] - ebase);
+        const uint32_t W = (a.dprime[r] + 31) / 32;
+        const uint32_t rsv = a.rsv_c[r];
+        uint32_t *region = a.pool + a.pool_off[r];
+        const unsigned long long e_vis = STATS ? a.e_all[r] : a.e_use[r];
+        uint32_t hs = (uint32_t)(2 * e_vis + 31) & ~31u;
+        hs = hs < 64 ? 64 : (hs > PS_HS ? PS_HS : hs);
+        for (uint32_t i = lane; i < hs; i += 32) {
+            keys[i] = EMPTY;
+            vals[i] = 0;
+        }
+        __syncwarp();
+        bool ovf = false;
+        visit_warp(ebase, d, !STATS, a.A_ent, a.A_pos, a.A_bit, a.B_off, a.B_ent,
+                   [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                       if (!tab_insert(keys, vals, hs, w, pass1_add(sdiff, bit))) ovf = true;
+                   });
+        __syncwarp();
+        uint32_t ncw = 0, npaper = 0;
+        if (__any_sync(FULL, ovf)) {
+            if (lane == 0) atomicOr(&a.cnt->err, CERR_HASH);
+        } else {
+            for (uint32_t base = 0; base < hs; base += 32) {
+                uint32_t i = base + lane;
+                bool cand = false, pap = false;
+                unsigned long long v = 0;
+                if (i < hs && keys[i] != EMPTY) {
+                    v = vals[i];
+                    pap = STATS && (v & M21) >= (unsigned long long)l;
+                    cand = keep_candidate(v, l);
+                }
+                uint32_t bal = __ballot_sync(FULL, cand);
+                if (cand) vals[i] = CAND | (ncw + __popc(bal & lt));
+                ncw += __popc(bal);
+                npaper += __popc(__ballot_sync(FULL, pap));
+            }
+            __syncwarp();
+            if (ncw > rsv) {
+                if (lane == 0) atomicOr(&a.cnt->err, CERR_RESERVE);
+                ncw = 0;
+            }
+            if (ncw > 0) {
+                for (uint32_t i = lane; i < 2 * W * ncw; i += 32) {
+                    uint32_t wd = i / ncw, c = i % ncw;
+                    region[(size_t)wd * rsv + c] = 0;
+                }
+                __syncwarp();
+                visit_warp(ebase, d, true, a.A_ent, a.A_pos, a.A_bit, a.B_off, a.B_ent,
+                           [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                               int sl = tab_find(keys, hs, w);
+                               if (sl < 0) return;
+                               unsigned long long v = vals[sl];
+                               if (!(v & CAND)) return;
+                               uint32_t c = (uint32_t)v;
+                               uint32_t m = 1u << (bit & 31);
+                               size_t wd = bit >> 5;
+                               atomicOr(&region[wd * rsv + c], m);
+                               if (sdiff) atomicOr(&region[(W + wd) * rsv + c], m);
+                           });
+            }
+        }
+        if (lane == 0) {
+            a.ncand[r] = ncw;
+            if (STATS) a.npaper[r] = npaper;
+        }
+        wedges += e_vis;
+        __syncwarp();
+    }
+    if (lane == 0 && wedges) atomicAdd(&a.cnt->wedges, wedges);
+}
+
+// ---- large anchors: one CTA per anchor, wedges flattened over the CTA
+
+constexpr int PL_THREADS = 512;
+constexpr int PL_WARPS = PL_THREADS / 32;
+constexpr int PL_HS = 7168;             // slots
+constexpr int PL_WCAP = PL_HS / 2;      // visited wedges per window (load <= 1/2)
+constexpr int PL_PCH = PL_THREADS;      // positions staged per chunk
+constexpr int PL_STAGE_WORDS = 4096;    // staged P/D words
+constexpr size_t PL_OFF_VALS = (size_t)PL_HS * 4;
+constexpr size_t PL_OFF_PST = PL_OFF_VALS + (size_t)PL_HS * 8;
+constexpr size_t PL_OFF_PPRE = PL_OFF_PST + (size_t)PL_PCH * 8;
+constexpr size_t PL_OFF_PINFO = PL_OFF_PPRE + (size_t)(PL_PCH + 4) * 4;
+constexpr size_t PL_OFF_STAGE = PL_OFF_PINFO + (size_t)PL_PCH * 4;
+constexpr size_t PL_SMEM = PL_OFF_STAGE + (size_t)PL_STAGE_WORDS * 4;
+
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *warp_tot,
+                                                        uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = PL_WARPS;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t wv = lane < NW ? warp_tot[lane] : 0u;
+        uint32_t wi = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < NW) warp_tot[lane] = wi - wv;
+        if (lane == NW - 1) *total = wi;
+    }
+    __syncthreads();
+    return warp_tot[warp] + incl - v;
+}
+
+// Visit the anchor's 2-hop entries of hash class `cls` with the whole CTA.
+// Positions are staged PL_PCH at a time; each thread takes every PL_THREADS-th
+// entry of the chunk's flattened suffixes. fn(w, sdiff, bit).
+template <typename F>
+__device__ __forceinline__ void visit_block(int64_t ebase, int d, bool useful_only, int lg_nw,
+                                            uint32_t cls, const TwohopArgs &a, int64_t *pst,
+                                            uint32_t *ppre, uint32_t *pinfo, uint32_t *warp_tot,
+                                            uint32_t *s_total, F fn) {
+    const int tid = threadIdx.x;
+    for (int c0 = 0; c0 < d; c0 += PL_PCH) {
+        const int nch = d - c0 < PL_PCH ? d - c0 : PL_PCH;
+        uint32_t len = 0;
+        if (tid < nch) {
+            int64_t e = ebase + c0 + tid;
+            uint32_t av = a.A_ent[e];
+            uint32_t y = av & VMASK;
+            uint32_t bit = a.A_bit[e];
+            int64_t st = a.B_off[y] + (int64_t)a.A_pos[e] + 1;
+            len = (uint32_t)(a.B_off[y + 1] - st);
+            if (useful_only && bit == EMPTY) len = 0;
+            pst[tid] = st;
+            pinfo[tid] = (av & 0x80000000u) | (bit == EMPTY ? NOBIT : bit);
+        }
+        uint32_t ex = block_excl_scan_u32(len, warp_tot, s_total);
+        ppre[tid] = ex;
         __syncthreads();
-        int item = s_item;
-        if (item >= (int)a.cnt->n_active) break;
+        const uint32_t total = *s_total;
+        for (uint32_t t = tid; t < total; t += PL_THREADS) {
+            uint32_t lo = 0, hi = (uint32_t)nch;  // largest j with ppre[j] <= t
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (ppre[mid] <= t) lo = mid; else hi = mid;
+            }
+            uint32_t ent = a.B_ent[pst[lo] + (t - ppre[lo])];
+            uint32_t w = ent & VMASK;
+            if (class_of(w, lg_nw) != cls) continue;
+            uint32_t info = pinfo[lo];
+            uint32_t bit = info & NOBIT;
+            fn(w, (info >> 31) ^ (ent >> 31), bit == NOBIT ? EMPTY : bit);
+        }
+        __syncthreads();
+    }
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *keys = (uint32_t *)smem_raw;
+    unsigned long long *vals = (unsigned long long *)(smem_raw + PL_OFF_VALS);
+    int64_t *pst = (int64_t *)(smem_raw + PL_OFF_PST);
+    uint32_t *ppre = (uint32_t *)(smem_raw + PL_OFF_PPRE);
+    uint32_t *pinfo = (uint32_t *)(smem_raw + PL_OFF_PINFO);
+    uint32_t *stage = (uint32_t *)(smem_raw + PL_OFF_STAGE);
+    __shared__ uint32_t warp_tot[PL_WARPS];
+    __shared__ uint32_t s_total;
+    __shared__ unsigned s_item, s_ncw, s_paper, s_ovf;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int l = a.l;
+    const unsigned n_big = a.cnt->n_big;
+    unsigned long long wedges = 0;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&a.cnt->head_large, 1u);
+        __syncthreads();
+        const unsigned item = s_item;
+        __syncthreads();
+        if (item >= n_big) break;
         const uint32_t r = a.order[item];
         const int64_t ebase = a.A_off[r];
         const int d = (int)(a.A_off[r + 1] - ebase);
@@ -330,19 +572,19 @@ __global__ void __launch_bounds__(PA_THREADS) k_twohop(TwohopArgs a) {
         uint32_t *region = a.pool + a.pool_off[r];
         const unsigned long long e_vis = STATS ? a.e_all[r] : a.e_use[r];
         int lg_nw = 0;
-        while (((unsigned long long)PA_WCAP << lg_nw) < e_vis) lg_nw++;
+        while (((unsigned long long)PL_WCAP << lg_nw) < e_vis) lg_nw++;
         uint32_t nc = 0, npaper = 0;
+        bool failed = false;
         for (int attempt = 0; attempt < 8; attempt++) {
             const uint32_t nw = 1u << lg_nw;
-            unsigned long long per = (e_vis + nw - 1) >> lg_nw;
-            int lg_hs = 6;
-            while ((1ull << lg_hs) < 2 * per && lg_hs < 12) lg_hs++;
-            const uint32_t hs = 1u << lg_hs;
+            const unsigned long long per = (e_vis + nw - 1) >> lg_nw;
+            uint32_t hs = (uint32_t)((2 * per + 31) & ~31ull);
+            hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
             nc = 0;
             npaper = 0;
             bool restart = false;
-            for (uint32_t cls = 0; cls < nw; cls++) {
-                for (uint32_t i = tid; i < hs; i += PA_THREADS) {
+            for (uint32_t cls = 0; cls < nw && !failed; cls++) {
+                for (uint32_t i = tid; i < hs; i += PL_THREADS) {
                     keys[i] = EMPTY;
                     vals[i] = 0;
                 }
@@ -352,42 +594,29 @@ __global__ void __launch_bounds__(PA_THREADS) k_twohop(TwohopArgs a) {
                     s_ovf = 0;
                 }
                 __syncthreads();
-                // pass 1: cnt[w] (low word: all positions, high word: useful)
-                visit_twohop(ebase, d, !STATS, lg_nw, cls, a.A_ent, a.A_pos, a.A_bit, a.B_off,
-                             a.B_ent, [&](uint32_t w, uint32_t, uint32_t bit) {
-                                 uint32_t sl = slot_of(w, lg_hs);
-                                 uint32_t probes = 0;
-                                 for (;;) {
-                                     uint32_t k = keys[sl];
-                                     if (k == w) break;
-                                     if (k == EMPTY) {
-                                         uint32_t old = atomicCAS(&keys[sl], EMPTY, w);
-                                         if (old == EMPTY || old == w) break;
-                                     }
-                                     sl = (sl + 1) & (hs - 1);
-                                     if (++probes >= hs) {
-                                         s_ovf = 1;
-                                         return;
-                                     }
-                                 }
-                                 atomicAdd(&vals[sl], bit != EMPTY ? 0x100000001ull : 1ull);
-                             });
-                __syncthreads();
+                visit_block(ebase, d, !STATS, lg_nw, cls, a, pst, ppre, pinfo, warp_tot, &s_total,
+                            [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                                if (!tab_insert(keys, vals, hs, w, pass1_add(sdiff, bit))) s_ovf = 1;
+                            });
                 if (s_ovf) {
                     restart = true;
                     break;
                 }
-                // candidate filter: cnt[w] >= l
-                for (uint32_t i = tid; i < hs; i += PA_THREADS) {
-                    if (keys[i] == EMPTY) continue;
-                    unsigned long long v = vals[i];
-                    if (STATS && (uint32_t)v >= (uint32_t)l) atomicAdd(&s_paper, 1u);
-                    if ((uint32_t)(v >> 32) >= (uint32_t)l) {
-                        uint32_t idx = atomicAdd(&s_ncw, 1u);
-                        vals[i] = (1ull << 63) | idx;
-                    } else {
-                        vals[i] = 0;
+                for (uint32_t base = 0; base < hs; base += PL_THREADS) {
+                    uint32_t i = base + tid;
+                    bool cand = false, pap = false;
+                    if (i < hs && keys[i] != EMPTY) {
+                        unsigned long long v = vals[i];
+                        pap = STATS && (v & M21) >= (unsigned long long)l;
+                        cand = keep_candidate(v, l);
                     }
+                    uint32_t bal = __ballot_sync(FULL, cand);
+                    uint32_t pb = __ballot_sync(FULL, pap);
+                    uint32_t wbase = 0;
+                    if (lane == 0 && bal) wbase = atomicAdd(&s_ncw, (unsigned)__popc(bal));
+                    if (lane == 0 && pb) atomicAdd(&s_paper, (unsigned)__popc(pb));
+                    wbase = __shfl_sync(FULL, wbase, 0);
+                    if (cand) vals[i] = CAND | (wbase + __popc(bal & ((1u << lane) - 1u)));
                 }
                 __syncthreads();
                 const uint32_t ncw = s_ncw;
@@ -395,42 +624,32 @@ __global__ void __launch_bounds__(PA_THREADS) k_twohop(TwohopArgs a) {
                 if (ncw > 0) {
                     if (nc + ncw > rsv) {
                         if (tid == 0) atomicOr(&a.cnt->err, CERR_RESERVE);
+                        failed = true;
                         __syncthreads();
                         break;
                     }
-                    const bool staged = 2ull * W * ncw <= (unsigned long long)PA_STAGE_WORDS;
-                    uint32_t *bits_base = staged ? stage : region + nc;
+                    const bool staged = 2ull * W * ncw <= (unsigned long long)PL_STAGE_WORDS;
+                    uint32_t *bb = staged ? stage : region + nc;
                     const uint32_t bstride = staged ? ncw : rsv;
-                    for (uint32_t i = tid; i < 2 * W * ncw; i += PA_THREADS) {
+                    for (uint32_t i = tid; i < 2 * W * ncw; i += PL_THREADS) {
                         uint32_t wd = i / ncw, c = i % ncw;
-                        bits_base[(size_t)wd * bstride + c] = 0;
+                        bb[(size_t)wd * bstride + c] = 0;
                     }
                     __syncthreads();
-                    // pass 2: P_w and D_w bits of candidates (useful positions)
-                    visit_twohop(ebase, d, true, lg_nw, cls, a.A_ent, a.A_pos, a.A_bit, a.B_off,
-                                 a.B_ent, [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
-                                     uint32_t sl = slot_of(w, lg_hs);
-                                     for (uint32_t probes = 0; probes < hs; probes++) {
-                                         uint32_t k = keys[sl];
-                                         if (k == w) {
-                                             unsigned long long v = vals[sl];
-                                             if (v >> 63) {
-                                                 uint32_t c = (uint32_t)v;
-                                                 uint32_t m = 1u << (bit & 31);
-                                                 size_t wd = bit >> 5;
-                                                 atomicOr(&bits_base[wd * bstride + c], m);
-                                                 if (sdiff)
-                                                     atomicOr(&bits_base[(W + wd) * bstride + c], m);
-                                             }
-                                             return;
-                                         }
-                                         if (k == EMPTY) return;
-                                         sl = (sl + 1) & (hs - 1);
-                                     }
-                                 });
-                    __syncthreads();
+                    visit_block(ebase, d, true, lg_nw, cls, a, pst, ppre, pinfo, warp_tot, &s_total,
+                                [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                                    int sl = tab_find(keys, hs, w);
+                                    if (sl < 0) return;
+                                    unsigned long long v = vals[sl];
+                                    if (!(v & CAND)) return;
+                                    uint32_t c = (uint32_t)v;
+                                    uint32_t m = 1u << (bit & 31);
+                                    size_t wd = bit >> 5;
+                                    atomicOr(&bb[wd * bstride + c], m);
+                                    if (sdiff) atomicOr(&bb[(W + wd) * bstride + c], m);
+                                });
                     if (staged) {
-                        for (uint32_t i = tid; i < 2 * W * ncw; i += PA_THREADS) {
+                        for (uint32_t i = tid; i < 2 * W * ncw; i += PL_THREADS) {
                             uint32_t wd = i / ncw, c = i % ncw;
                             region[(size_t)wd * rsv + nc + c] = stage[i];
                         }
@@ -439,16 +658,20 @@ __global__ void __launch_bounds__(PA_THREADS) k_twohop(TwohopArgs a) {
                 }
                 __syncthreads();
             }
-            if (!restart) break;
+            if (!restart || failed) break;
             lg_nw++;
-            if (attempt == 7 && tid == 0) atomicOr(&a.cnt->err, CERR_HASH);
+            if (attempt == 7) {
+                if (tid == 0) atomicOr(&a.cnt->err, CERR_HASH);
+                failed = true;
+            }
             __syncthreads();
         }
+        if (failed) nc = 0;
         if (tid == 0) {
             a.ncand[r] = nc;
             if (STATS) a.npaper[r] = npaper;
+            wedges += e_vis;
         }
-        if (tid == 0) wedges += e_vis;
         __syncthreads();
     }
     if (tid == 0 && wedges) atomicAdd(&a.cnt->wedges, wedges);
@@ -643,6 +866,7 @@ constexpr int PB_THREADS = 256;
 constexpr int PB_WARPS = PB_THREADS / 32;
 constexpr int PB_SMEM_WORDS = 24576;  // 96 KB of staged P/D words
 constexpr size_t PB_SMEM = PB_SMEM_WORDS * 4;
+constexpr int SCRATCH_SLOTS = 7;  // per-warp mask slots for wide anchors (>= max(R, 6))
 
 struct TupleArgs {
     const uint32_t *ncand, *dprime, *rsv_c;
@@ -1005,6 +1229,254 @@ __device__ void unit_wide(const Masks &m, uint32_t *scratch, uint32_t wmax, uint
     }
 }
 
+// ---- type parts (R <= 3). By Lemma 1 and its converse, every v of a
+// balanced biclique's other side has the same type relative to the anchor,
+// so a prefix of partners is carried as its type parts: the masks of common
+// neighbours sharing one type vector, kept only while they hold at least l
+// bits. Extending by a partner m splits each part P into P & P_m & ~D_m and
+// P & P_m & D_m; at the last partner each child adds binom(popc, l). Parts
+// below l bits are dropped, which drops only zero binomials.
+
+// Split one part y (already ANDed with P_m) by D_m and add the binomials.
+template <int WN>
+__device__ __forceinline__ void close_part(const Masks &m, const uint32_t (&y)[WN], uint32_t c,
+                                           int l, Acc &acc, unsigned *err) {
+    uint32_t n = 0;
+#pragma unroll
+    for (int w = 0; w < WN; w++) n += __popc(y[w]);
+    acc.words += m.W;
+    if ((int)n < l) return;
+    uint32_t x1 = 0;
+#pragma unroll
+    for (int w = 0; w < WN; w++)
+        if (w < (int)m.W) x1 += __popc(y[w] & m.D(w, c));
+    acc.words += m.W;
+    acc.leaves++;
+    binom_add(acc.sum, x1, l, err);
+    binom_add(acc.sum, n - x1, l, err);
+}
+
+template <int WN>
+__device__ void parts_r1(const Masks &m, uint32_t jc, int l, Acc &acc, unsigned *err) {
+    const uint32_t c = jc * 32 + (threadIdx.x & 31);
+    if (c >= m.nc) return;
+    acc.tested++;
+    uint32_t y[WN];
+#pragma unroll
+    for (int w = 0; w < WN; w++) y[w] = w < (int)m.W ? m.P(w, c) : 0u;
+    close_part<WN>(m, y, c, l, acc, err);
+}
+
+// Type parts of candidate i: A0 = P_i & ~D_i (same sign), A1 = P_i & D_i.
+template <int WN>
+__device__ __forceinline__ uint32_t parts_of(const Masks &m, uint32_t i, uint32_t (&A0)[WN],
+                                             uint32_t (&A1)[WN], int l) {
+    uint32_t n0 = 0, n1 = 0;
+#pragma unroll
+    for (int w = 0; w < WN; w++) {
+        uint32_t p = w < (int)m.W ? m.P(w, i) : 0u;
+        uint32_t d = w < (int)m.W ? m.D(w, i) : 0u;
+        A0[w] = p & ~d;
+        A1[w] = p & d;
+        n0 += __popc(A0[w]);
+        n1 += __popc(A1[w]);
+    }
+    return ((int)n0 >= l ? 1u : 0u) | ((int)n1 >= l ? 2u : 0u);
+}
+
+template <int WN>
+__device__ void parts_r2(const Masks &m, uint32_t i, uint32_t jc, int l, Acc &acc,
+                         unsigned *err) {
+    uint32_t A0[WN], A1[WN];
+    const uint32_t va = parts_of<WN>(m, i, A0, A1, l);
+    if (!va) return;
+    const uint32_t j = i + 1 + jc * 32 + (threadIdx.x & 31);
+    if (j >= m.nc) return;
+    acc.tested++;
+    uint32_t pj[WN];
+#pragma unroll
+    for (int w = 0; w < WN; w++) pj[w] = w < (int)m.W ? m.P(w, j) : 0u;
+    if (va & 1u) {
+        uint32_t y[WN];
+#pragma unroll
+        for (int w = 0; w < WN; w++) y[w] = A0[w] & pj[w];
+        close_part<WN>(m, y, j, l, acc, err);
+    }
+    if (va & 2u) {
+        uint32_t y[WN];
+#pragma unroll
+        for (int w = 0; w < WN; w++) y[w] = A1[w] & pj[w];
+        close_part<WN>(m, y, j, l, acc, err);
+    }
+}
+
+template <int WN>
+__device__ void parts_r3(const Masks &m, uint32_t i, uint32_t jc, int l, Acc &acc,
+                         unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    uint32_t A0[WN], A1[WN];
+    const uint32_t va = parts_of<WN>(m, i, A0, A1, l);
+    if (!va) return;
+    const uint32_t j = i + 1 + jc * 32 + lane;
+    const bool valid = j + 1 < m.nc;  // room for a third partner
+    uint32_t vb = 0;
+    if (valid) {
+        acc.tested++;
+        uint32_t n[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int w = 0; w < WN; w++) {
+            uint32_t p = w < (int)m.W ? m.P(w, j) : 0u;
+            uint32_t d = w < (int)m.W ? m.D(w, j) : 0u;
+            n[0] += __popc(A0[w] & p & ~d);
+            n[1] += __popc(A0[w] & p & d);
+            n[2] += __popc(A1[w] & p & ~d);
+            n[3] += __popc(A1[w] & p & d);
+        }
+        acc.words += 4 * m.W;
+#pragma unroll
+        for (int b = 0; b < 4; b++) vb |= ((int)n[b] >= l ? 1u : 0u) << b;
+        vb &= ((va & 1u) ? 3u : 0u) | ((va & 2u) ? 12u : 0u);
+    }
+    uint32_t bal = __ballot_sync(FULL, vb != 0);
+    while (bal) {
+        const int s = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const uint32_t js = i + 1 + jc * 32 + s;
+        const uint32_t vbs = __shfl_sync(FULL, vb, s);
+        uint32_t B[4][WN];
+#pragma unroll
+        for (int w = 0; w < WN; w++) {
+            uint32_t p = w < (int)m.W ? m.P(w, js) : 0u;
+            uint32_t d = w < (int)m.W ? m.D(w, js) : 0u;
+            B[0][w] = A0[w] & p & ~d;
+            B[1][w] = A0[w] & p & d;
+            B[2][w] = A1[w] & p & ~d;
+            B[3][w] = A1[w] & p & d;
+        }
+        for (uint32_t mb = js + 1; mb < m.nc; mb += 32) {
+            const uint32_t c = mb + lane;
+            if (c >= m.nc) continue;
+            acc.tested++;
+            uint32_t pc[WN];
+#pragma unroll
+            for (int w = 0; w < WN; w++) pc[w] = w < (int)m.W ? m.P(w, c) : 0u;
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                if (!((vbs >> b) & 1u)) continue;
+                uint32_t y[WN];
+#pragma unroll
+                for (int w = 0; w < WN; w++) y[w] = B[b][w] & pc[w];
+                close_part<WN>(m, y, c, l, acc, err);
+            }
+        }
+    }
+}
+
+// ---- type parts for wide anchors: parts live in the warp's scratch
+// (slot k at scratch + k * wmax), words streamed.
+
+__device__ __forceinline__ void wide_close(const Masks &m, const uint32_t *part, uint32_t c,
+                                           int l, Acc &acc, unsigned *err) {
+    uint32_t n = 0, x1 = 0;
+    for (uint32_t w = 0; w < m.W; w++) {
+        uint32_t y = part ? (part[w] & m.P(w, c)) : m.P(w, c);
+        n += __popc(y);
+        x1 += __popc(y & m.D(w, c));
+    }
+    acc.words += 2 * m.W;
+    if ((int)n < l) return;
+    acc.leaves++;
+    binom_add(acc.sum, x1, l, err);
+    binom_add(acc.sum, n - x1, l, err);
+}
+
+// Writes the parts of candidate i to scratch slots 0, 1; returns viability.
+__device__ __forceinline__ uint32_t wide_parts_of(const Masks &m, uint32_t i, uint32_t *scratch,
+                                                  uint32_t wmax, int l) {
+    const int lane = threadIdx.x & 31;
+    uint32_t n0 = 0, n1 = 0;
+    __syncwarp();
+    for (uint32_t w = lane; w < m.W; w += 32) {
+        uint32_t p = m.P(w, i), d = m.D(w, i);
+        scratch[w] = p & ~d;
+        scratch[wmax + w] = p & d;
+        n0 += __popc(p & ~d);
+        n1 += __popc(p & d);
+    }
+    __syncwarp();
+    n0 = __reduce_add_sync(FULL, n0);
+    n1 = __reduce_add_sync(FULL, n1);
+    return ((int)n0 >= l ? 1u : 0u) | ((int)n1 >= l ? 2u : 0u);
+}
+
+__device__ void wide_r1(const Masks &m, uint32_t jc, int l, Acc &acc, unsigned *err) {
+    const uint32_t c = jc * 32 + (threadIdx.x & 31);
+    if (c >= m.nc) return;
+    acc.tested++;
+    wide_close(m, nullptr, c, l, acc, err);
+}
+
+__device__ void wide_r2(const Masks &m, uint32_t *scratch, uint32_t wmax, uint32_t i, uint32_t jc,
+                        int l, Acc &acc, unsigned *err) {
+    const uint32_t va = wide_parts_of(m, i, scratch, wmax, l);
+    if (!va) return;
+    const uint32_t j = i + 1 + jc * 32 + (threadIdx.x & 31);
+    if (j >= m.nc) return;
+    acc.tested++;
+    if (va & 1u) wide_close(m, scratch, j, l, acc, err);
+    if (va & 2u) wide_close(m, scratch + wmax, j, l, acc, err);
+}
+
+__device__ void wide_r3(const Masks &m, uint32_t *scratch, uint32_t wmax, uint32_t i, uint32_t jc,
+                        int l, Acc &acc, unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t va = wide_parts_of(m, i, scratch, wmax, l);
+    if (!va) return;
+    const uint32_t j = i + 1 + jc * 32 + lane;
+    const bool valid = j + 1 < m.nc;
+    uint32_t vb = 0;
+    if (valid) {
+        acc.tested++;
+        uint32_t n[4] = {0, 0, 0, 0};
+        for (uint32_t w = 0; w < m.W; w++) {
+            uint32_t p = m.P(w, j), d = m.D(w, j);
+            uint32_t a0 = scratch[w], a1 = scratch[wmax + w];
+            n[0] += __popc(a0 & p & ~d);
+            n[1] += __popc(a0 & p & d);
+            n[2] += __popc(a1 & p & ~d);
+            n[3] += __popc(a1 & p & d);
+        }
+        acc.words += 4 * m.W;
+        for (int b = 0; b < 4; b++) vb |= ((int)n[b] >= l ? 1u : 0u) << b;
+        vb &= ((va & 1u) ? 3u : 0u) | ((va & 2u) ? 12u : 0u);
+    }
+    uint32_t bal = __ballot_sync(FULL, vb != 0);
+    while (bal) {
+        const int s = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const uint32_t js = i + 1 + jc * 32 + s;
+        const uint32_t vbs = __shfl_sync(FULL, vb, s);
+        __syncwarp();
+        for (uint32_t w = lane; w < m.W; w += 32) {
+            uint32_t p = m.P(w, js), d = m.D(w, js);
+            uint32_t a0 = scratch[w], a1 = scratch[wmax + w];
+            scratch[(2 + 0) * (size_t)wmax + w] = a0 & p & ~d;
+            scratch[(2 + 1) * (size_t)wmax + w] = a0 & p & d;
+            scratch[(2 + 2) * (size_t)wmax + w] = a1 & p & ~d;
+            scratch[(2 + 3) * (size_t)wmax + w] = a1 & p & d;
+        }
+        __syncwarp();
+        for (uint32_t mb = js + 1; mb < m.nc; mb += 32) {
+            const uint32_t c = mb + lane;
+            if (c >= m.nc) continue;
+            acc.tested++;
+            for (int b = 0; b < 4; b++)
+                if ((vbs >> b) & 1u) wide_close(m, scratch + (2 + b) * (size_t)wmax, c, l, acc, err);
+        }
+        __syncwarp();
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
@@ -1014,7 +1486,8 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned *err = &a.cnt->err;
     uint32_t *scratch =
-        a.wide_scratch ? a.wide_scratch + ((size_t)blockIdx.x * PB_WARPS + warp) * R * a.wmax : nullptr;
+        a.wide_scratch ? a.wide_scratch + ((size_t)blockIdx.x * PB_WARPS + warp) * SCRATCH_SLOTS * a.wmax
+                       : nullptr;
     for (;;) {
         if (tid == 0) s_item = (int)atomicAdd(&a.cnt->head_b, 1u);
         __syncthreads();
@@ -1077,11 +1550,31 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
                 i = it.i0 + lo;
                 jc = u - s_rowpre[lo];
             }
-            if (W <= 1) unit_narrow<R, 1>(m, i, jc, a.l, acc, err);
-            else if (W <= 2) unit_narrow<R, 2>(m, i, jc, a.l, acc, err);
-            else if (W <= 4) unit_narrow<R, 4>(m, i, jc, a.l, acc, err);
-            else if (W <= 8) unit_narrow<R, 8>(m, i, jc, a.l, acc, err);
-            else unit_wide<R>(m, scratch, a.wmax, i, jc, a.l, acc, err);
+            if constexpr (R == 1) {
+                if (W <= 1) parts_r1<1>(m, jc, a.l, acc, err);
+                else if (W <= 2) parts_r1<2>(m, jc, a.l, acc, err);
+                else if (W <= 4) parts_r1<4>(m, jc, a.l, acc, err);
+                else if (W <= 8) parts_r1<8>(m, jc, a.l, acc, err);
+                else wide_r1(m, jc, a.l, acc, err);
+            } else if constexpr (R == 2) {
+                if (W <= 1) parts_r2<1>(m, i, jc, a.l, acc, err);
+                else if (W <= 2) parts_r2<2>(m, i, jc, a.l, acc, err);
+                else if (W <= 4) parts_r2<4>(m, i, jc, a.l, acc, err);
+                else if (W <= 8) parts_r2<8>(m, i, jc, a.l, acc, err);
+                else wide_r2(m, scratch, a.wmax, i, jc, a.l, acc, err);
+            } else if constexpr (R == 3) {
+                if (W <= 1) parts_r3<1>(m, i, jc, a.l, acc, err);
+                else if (W <= 2) parts_r3<2>(m, i, jc, a.l, acc, err);
+                else if (W <= 4) parts_r3<4>(m, i, jc, a.l, acc, err);
+                else if (W <= 8) parts_r3<8>(m, i, jc, a.l, acc, err);
+                else wide_r3(m, scratch, a.wmax, i, jc, a.l, acc, err);
+            } else {
+                if (W <= 1) unit_narrow<R, 1>(m, i, jc, a.l, acc, err);
+                else if (W <= 2) unit_narrow<R, 2>(m, i, jc, a.l, acc, err);
+                else if (W <= 4) unit_narrow<R, 4>(m, i, jc, a.l, acc, err);
+                else if (W <= 8) unit_narrow<R, 8>(m, i, jc, a.l, acc, err);
+                else unit_wide<R>(m, scratch, a.wmax, i, jc, a.l, acc, err);
+            }
         }
         U128 ws = warp_sum_u128(acc.sum);
         if (lane == 0 && (ws.lo | ws.hi)) {
@@ -1141,8 +1634,10 @@ void ensure_kernel_attrs() {
     static bool done = false;
     std::lock_guard<std::mutex> lock(mu);
     if (done) return;
-    SBC_CUDA(cudaFuncSetAttribute(k_twohop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PA_SMEM));
-    SBC_CUDA(cudaFuncSetAttribute(k_twohop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PA_SMEM));
+    SBC_CUDA(cudaFuncSetAttribute(k_twohop_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PS_SMEM));
+    SBC_CUDA(cudaFuncSetAttribute(k_twohop_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PS_SMEM));
+    SBC_CUDA(cudaFuncSetAttribute(k_twohop_large<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL_SMEM));
+    SBC_CUDA(cudaFuncSetAttribute(k_twohop_large<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL_SMEM));
     set_tuple_attr<1>();
     set_tuple_attr<2>();
     set_tuple_attr<3>();
@@ -1222,6 +1717,9 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     const Orient &o = g->side[side];
     const int64_t nnz = g->nnz;
     const int B = 256;
+    if (o.max_deg_x >= (1ll << 21))
+        fail(SBC_E_UNSUPPORTED, "anchor-side degree %lld exceeds the 2^21 - 1 limit of the 2-hop counters",
+             (long long)o.max_deg_x);
 
     unsigned long long lim[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int i = 2; i <= 8; i++) lim[i] = binom64_limit(i);
@@ -1237,7 +1735,7 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     k_plan<<<grid_for(nX * 32, B), B, 0, s>>>(o.A_off.ptr, o.A_ent.ptr, o.A_pos.ptr, o.B_off.ptr, nX,
                                               R, l, shard, nshard, paper ? 1 : 0, A_bit.ptr,
                                               dprime.ptr, e_use.ptr, e_all.ptr, rsv_c.ptr,
-                                              pool_off.ptr, skey.ptr, sval.ptr, cnt.ptr);
+                                              pool_off.ptr, skey.ptr, sval.ptr, cnt.ptr, SMALL_E);
     SBC_LAUNCHED();
     g_launches++;
     scan_exclusive_i64(pool_off.ptr, pool_off.ptr, nX + 1, dtot.ptr, s);
@@ -1272,13 +1770,25 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
         ta.npaper = paper ? npaper.ptr : nullptr;
         ta.cnt = cnt.ptr;
         ta.l = l;
-        const void *fn = paper ? (const void *)k_twohop<true> : (const void *)k_twohop<false>;
-        int ga = sms * blocks_per_sm(fn, PA_THREADS, PA_SMEM);
-        if ((int64_t)ga > (int64_t)hc.n_active) ga = (int)hc.n_active;
-        if (paper) k_twohop<true><<<ga, PA_THREADS, PA_SMEM, s>>>(ta);
-        else k_twohop<false><<<ga, PA_THREADS, PA_SMEM, s>>>(ta);
-        SBC_LAUNCHED();
-        g_launches++;
+        if (hc.n_big > 0) {
+            const void *fn = paper ? (const void *)k_twohop_large<true> : (const void *)k_twohop_large<false>;
+            int ga = sms * blocks_per_sm(fn, PL_THREADS, PL_SMEM);
+            if ((int64_t)ga > (int64_t)hc.n_big) ga = (int)hc.n_big;
+            if (paper) k_twohop_large<true><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
+            else k_twohop_large<false><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
+            SBC_LAUNCHED();
+            g_launches++;
+        }
+        if (hc.n_active > hc.n_big) {
+            const void *fn = paper ? (const void *)k_twohop_small<true> : (const void *)k_twohop_small<false>;
+            int gs = sms * blocks_per_sm(fn, PS_THREADS, PS_SMEM);
+            int64_t need = ((int64_t)hc.n_active - hc.n_big + PS_WARPS - 1) / PS_WARPS;
+            if ((int64_t)gs > need) gs = (int)need;
+            if (paper) k_twohop_small<true><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
+            else k_twohop_small<false><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
+            SBC_LAUNCHED();
+            g_launches++;
+        }
     }
     tm.mark(2, s);
 
@@ -1335,7 +1845,7 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
         uint32_t wmax = (uint32_t)((o.max_deg_x + 31) / 32);
         int grid = gb;
         if ((int64_t)grid > n_items) grid = (int)n_items;
-        DevBuf<uint32_t> scratch(wmax > 8 ? (size_t)grid * PB_WARPS * R * wmax : 0, s);
+        DevBuf<uint32_t> scratch(wmax > 8 ? (size_t)grid * PB_WARPS * SCRATCH_SLOTS * wmax : 0, s);
         TupleArgs tu;
         tu.ncand = ncand.ptr;
         tu.dprime = dprime.ptr;
