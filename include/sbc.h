@@ -174,6 +174,29 @@ sbc_status sbc_count_csr(int64_t n_u, int64_t n_v, int64_t nnz, const void *row_
                          const int32_t *cols, const void *signs, uint32_t flags, int p, int q,
                          sbc_u128 *out, void *stream);
 
+/*
+ * sbc_count_csr without any device allocation, for callers that cannot call
+ * cudaMalloc (a fixed device-memory plan, a loop that must not enter the
+ * allocator). No counterpart in the paper: same arguments and result as
+ * sbc_count_csr, but every device buffer of the call is carved from one
+ * fixed array of SBC_NOALLOC_SCRATCH_BYTES in device memory that the library
+ * holds on every GPU it is loaded on, and the call makes no cudaMalloc,
+ * cudaFree or other allocating call. Inputs may be host or device pointers
+ * (SBC_DEVICE_PTRS). Limits: at most SBC_NOALLOC_MAX_VERTICES per side and
+ * SBC_NOALLOC_MAX_EDGES edges (else SBC_E_INVAL); a graph whose counting
+ * needs more scratch than the array holds gives SBC_E_NOMEM. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Calls share the array and
+ * are serialised by a lock inside the library; calls from other processes
+ * that overlap on the same GPU memory would race.
+ */
+#define SBC_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define SBC_NOALLOC_MAX_VERTICES 65536
+#define SBC_NOALLOC_MAX_EDGES 65536
+sbc_status sbc_count_csr_noalloc(int64_t n_u, int64_t n_v, int64_t nnz, const void *row_offsets,
+                                 const int32_t *cols, const void *signs, uint32_t flags, int p,
+                                 int q, sbc_u128 *out, void *stream);
+
 /* Human-readable message for the last non-OK status on this thread. */
 const char *sbc_last_error(void);
 

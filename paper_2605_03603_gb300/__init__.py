@@ -20,7 +20,7 @@ from . import build as _build
 __all__ = [
     "SbcError", "Graph", "sbc_graph_create", "sbc_graph_destroy", "sbc_graph_info",
     "sbc_count", "sbc_count_ex", "sbc_count_csr", "sbc_last_error", "sbc_version",
-    "sbc_launch_count",
+    "sbc_launch_count", "sbc_count_csr_noalloc",
     "lib", "LIB_PATH",
 ]
 
@@ -108,6 +108,14 @@ _declare("sbc_count_csr", ctypes.c_int,
 _declare("sbc_last_error", ctypes.c_char_p, [])
 _declare("sbc_version", ctypes.c_char_p, [])
 _declare("sbc_launch_count", ctypes.c_uint64, [])
+_declare("sbc_count_csr_noalloc", ctypes.c_int,
+         [_i64, _i64, _i64, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+          ctypes.POINTER(U128), _vp])
+
+# sbc_count_csr_noalloc limits (include/sbc.h)
+SBC_NOALLOC_SCRATCH_BYTES = 32 << 20
+SBC_NOALLOC_MAX_VERTICES = 65536
+SBC_NOALLOC_MAX_EDGES = 65536
 
 
 def sbc_launch_count() -> int:
@@ -277,6 +285,24 @@ def sbc_count_csr(n_u: int, n_v: int, row_offsets, cols, signs, p: int, q: int,
     out = U128()
     _check(lib.sbc_count_csr(n_u, n_v, int(cols.shape[0]), off_p, col_p, sg_p, flags, p, q,
                              ctypes.byref(out), _stream_ptr(stream)))
+    return out.value()
+
+
+def sbc_count_csr_noalloc(n_u: int, n_v: int, row_offsets, cols, signs, p: int, q: int,
+                          sign_bits: bool = False, stream=None) -> int:
+    """sbc_count_csr for callers that cannot allocate device memory: the
+    library takes all scratch from a fixed device array (see include/sbc.h)."""
+    off_p, off_dev = _ptr(row_offsets)
+    col_p, _ = _ptr(cols)
+    sg_p, _ = _ptr(signs)
+    flags = SBC_OFFS_I64 if str(row_offsets.dtype).endswith("int64") else 0
+    if sign_bits:
+        flags |= SBC_SIGN_BITS
+    if off_dev:
+        flags |= SBC_DEVICE_PTRS
+    out = U128()
+    _check(lib.sbc_count_csr_noalloc(n_u, n_v, int(cols.shape[0]), off_p, col_p, sg_p, flags, p,
+                                     q, ctypes.byref(out), _stream_ptr(stream)))
     return out.value()
 
 

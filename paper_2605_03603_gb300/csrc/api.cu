@@ -11,6 +11,7 @@ std::atomic<int64_t> g_launches{0};
 
 namespace {
 thread_local std::string t_err;
+thread_local Arena *t_arena = nullptr;
 sbc_alloc_fn g_alloc = nullptr;
 sbc_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
@@ -27,8 +28,23 @@ void fail(sbc_status s, const char *fmt, ...) {
     throw SbcError(s, buf);
 }
 
+void set_thread_arena(Arena *a) { t_arena = a; }
+bool thread_arena_active() { return t_arena != nullptr; }
+
 void *dev_alloc(size_t bytes, cudaStream_t s) {
     void *p = nullptr;
+    if (t_arena) {
+        const size_t need = (bytes + 255) & ~(size_t)255;
+        if (t_arena->top + need > t_arena->size)
+            fail(SBC_E_NOMEM,
+                 "the graph needs more than the %zu bytes of fixed scratch of the "
+                 "no-allocation entry point (%zu in use, %zu more requested)",
+                 t_arena->size, t_arena->top, need);
+        p = t_arena->base + t_arena->top;
+        t_arena->top += need;
+        if (t_arena->top > t_arena->peak) t_arena->peak = t_arena->top;
+        return p;
+    }
     if (g_alloc) {
         p = g_alloc(bytes, (void *)s, g_alloc_ctx);
         if (!p) fail(SBC_E_NOMEM, "allocator hook returned NULL for %zu bytes", bytes);
@@ -44,6 +60,11 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
 
 void dev_free(void *p, size_t bytes, cudaStream_t s) {
     if (!p) return;
+    if (t_arena) {
+        const size_t need = (bytes + 255) & ~(size_t)255;
+        if ((char *)p + need == t_arena->base + t_arena->top) t_arena->top -= need;
+        return;
+    }
     if (g_free) {
         g_free(p, bytes, (void *)s, g_alloc_ctx);
         return;

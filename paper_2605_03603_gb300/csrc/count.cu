@@ -1708,7 +1708,7 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     if (opts && opts->per_anchor && nX > 0) memset(opts->per_anchor, 0, sizeof(sbc_u128) * (size_t)nX);
     if (g->nnz == 0 || nX == 0) return;
     ensure_kernel_attrs();
-    EventTimer tm(stats != nullptr);
+    EventTimer tm(stats != nullptr && !thread_arena_active());
     tm.mark(0, s);
     {
         std::lock_guard<std::mutex> lock(g->mu);

@@ -43,6 +43,17 @@ void set_last_error(const std::string &msg);
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
 
+// A caller-provided region of device memory that dev_alloc carves from (a
+// stack: blocks freed in reverse order are reclaimed) while it is installed on
+// the calling thread with set_thread_arena. Only the no-allocation entry point
+// installs one.
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, top = 0, peak = 0;
+};
+void set_thread_arena(Arena *a);
+bool thread_arena_active();
+
 // Owning device buffer (stream-ordered allocation).
 template <typename T>
 struct DevBuf {
@@ -159,6 +170,10 @@ int sm_count();
 
 // Kernel launches issued by the library since load (for reporting).
 extern std::atomic<int64_t> g_launches;
+
+// Upload, validate and prepare a graph (graph.cu).
+sbc_graph *create_graph(int64_t n_u, int64_t n_v, int64_t nnz, const void *row_offsets,
+                        const int32_t *cols, const void *signs, uint32_t flags, cudaStream_t s);
 
 // Count driver: defined in count.cu.
 void count_graph(const sbc_graph *g, int p, int q, const sbc_count_opts *opts,
