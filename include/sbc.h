@@ -116,6 +116,9 @@ sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
                                            exactly as printed (cnt over every neighbour)
                                            and report sum binom(|C(u)|, k-1) in
                                            sbc_count_stats.anchor_tuples */
+#define SBC_COUNT_CANDIDATE_SIDE (1 << 1) /* enumerate candidate subsets for every anchor */
+#define SBC_COUNT_POSITION_SIDE (1 << 2)  /* enumerate position subsets wherever they fit
+                                             (default: the cheaper side per anchor) */
 
 typedef struct {
     int32_t anchor_side;  /* SBC_SIDE_AUTO, SBC_SIDE_U or SBC_SIDE_V */

@@ -691,16 +691,23 @@ __device__ __forceinline__ unsigned long long binom_sat(unsigned long long n, in
     return r;
 }
 
+// A work item of one anchor. Candidate side: rows [i0, i1) of first
+// partners, all their units when u1 == 0, else units [u0, u1) of row i0.
+// Position side (u1 == POS_ITEM): first positions [i0, i1).
 struct Item {
-    uint32_t anchor, i0, i1, u0, u1;  // u1 == 0: all units of rows [i0, i1)
+    uint32_t anchor, i0, i1, u0, u1;
 };
+constexpr uint32_t POS_ITEM = 0xFFFFFFFFu;
+constexpr int POS_MAX_WORDS = 128;  // candidate words of a position-side mask (4 per lane)
 
 constexpr int ROWS_MAX = 1024;
+constexpr int PB_SMEM_WORDS_PLAN = 24576;  // staged words of the tuple kernel (PB_SMEM_WORDS)
 
 struct ItemArgs {
     const uint32_t *ncand, *npaper, *dprime;
     int64_t nX;
-    int R;
+    int R, l;
+    int method;  // 0: cheaper side per anchor, 1: candidate side, 2: position side where it fits
     unsigned long long item_cost;
     const int64_t *item_off;  // emit pass
     int64_t *item_cnt;        // count pass (nX + 1 entries)
@@ -727,6 +734,53 @@ __device__ __forceinline__ unsigned long long unit_cost(uint32_t nc, uint32_t i,
     }
     unsigned long long c = s * W;
     return (W && c / W != s) ? 0xFFFFFFFFFFFFFFFFull : c;
+}
+
+// Position-side enumeration of one anchor (see k_tuples): l-subsets Q of the
+// anchor's useful positions, each with N_Q candidates whose same-sign or
+// different-sign part of L[w] contains Q; the anchor adds sum over Q of
+// binom(N_Q, R). Cost in the candidate-side units (mask words x tuples):
+// 32 lanes x 3 steps x words per lane for every prefix node.
+__device__ __forceinline__ bool pos_fits(uint32_t nc, uint32_t dp, int l) {
+    const uint32_t wc = (nc + 31) / 32;
+    return dp >= (uint32_t)l && wc <= (uint32_t)POS_MAX_WORDS &&
+           2ull * dp * wc <= (unsigned long long)PB_SMEM_WORDS_PLAN;
+}
+
+__device__ __forceinline__ unsigned long long pos_row_cost(uint32_t nc, uint32_t dp, uint32_t q1,
+                                                           int l) {
+    const unsigned long long wpl = ((nc + 31) / 32 + 31) / 32;
+    unsigned long long nodes = 0;
+    for (int i = 0; i < l; i++) {
+        unsigned long long t = binom_sat(dp - 1 - q1, i);
+        nodes = (nodes + t < nodes) ? 0xFFFFFFFFFFFFFFFFull : nodes + t;
+    }
+    unsigned long long c = nodes * 96ull * wpl;
+    return (c / (96ull * wpl) != nodes) ? 0xFFFFFFFFFFFFFFFFull : c;
+}
+
+__device__ __forceinline__ unsigned long long pos_cost(uint32_t nc, uint32_t dp, int l) {
+    const unsigned long long wpl = ((nc + 31) / 32 + 31) / 32;
+    unsigned long long nodes = 0;
+    for (int i = 1; i <= l; i++) {
+        unsigned long long t = binom_sat(dp, i);
+        nodes = (nodes + t < nodes) ? 0xFFFFFFFFFFFFFFFFull : nodes + t;
+    }
+    unsigned long long c = nodes * 96ull * wpl;
+    return (c / (96ull * wpl) != nodes) ? 0xFFFFFFFFFFFFFFFFull : c;
+}
+
+__device__ __forceinline__ unsigned long long cand_cost(uint32_t nc, uint32_t W, int R) {
+    unsigned long long t = binom_sat(nc, R);
+    unsigned long long c = t * (W ? W : 1);
+    return (W > 1 && c / W != t) ? 0xFFFFFFFFFFFFFFFFull : c;
+}
+
+// True when the anchor takes the position side (cheaper, or forced).
+__device__ __forceinline__ bool use_pos(uint32_t nc, uint32_t dp, int R, int l, int method) {
+    if (method == 1 || nc < (uint32_t)R || !pos_fits(nc, dp, l)) return false;
+    if (method == 2) return true;
+    return pos_cost(nc, dp, l) < cand_cost(nc, (dp + 31) / 32, R);
 }
 
 // Anchor cost, anchor tuple counts. Thread per anchor.
@@ -761,7 +815,8 @@ __global__ void k_anchor_cost(ItemArgs a) {
         if (nc >= (uint32_t)a.R) {
             unsigned long long t = binom_sat(nc, a.R);
             to.add(t);
-            unsigned long long c = t * (W ? W : 1);
+            unsigned long long c = use_pos(nc, a.dprime[r], a.R, a.l, a.method) ? pos_cost(nc, a.dprime[r], a.l)
+                                                                     : cand_cost(nc, W, a.R);
             cost = (cost + c < cost) ? 0xFFFFFFFFFFFFFFFFull : cost + c;
         }
     }
@@ -806,7 +861,23 @@ __global__ void k_items(ItemArgs a) {
             }
             n++;
         };
-        if (nc >= (uint32_t)R && nc > 0) {
+        const uint32_t dp = a.dprime[r];
+        if (nc >= (uint32_t)R && nc > 0 && use_pos(nc, dp, R, a.l, a.method)) {
+            const uint32_t rows = dp - a.l + 1;
+            const unsigned long long cap = 4 * a.item_cost;
+            uint32_t rb = 0;
+            unsigned long long acc = 0;
+            for (uint32_t q1 = 0; q1 < rows; q1++) {
+                unsigned long long c = pos_row_cost(nc, dp, q1, a.l);
+                if (q1 > rb && (acc + c > cap || q1 - rb >= (uint32_t)ROWS_MAX)) {
+                    emit(rb, q1, 0, POS_ITEM, acc);
+                    rb = q1;
+                    acc = 0;
+                }
+                acc = (acc + c < acc) ? 0xFFFFFFFFFFFFFFFFull : acc + c;
+            }
+            emit(rb, rows, 0, POS_ITEM, acc);
+        } else if (nc >= (uint32_t)R && nc > 0) {
             if (R == 1) {
                 uint32_t units = (nc + 31) / 32;
                 unsigned long long per = 32ull * W, acc = 0;
@@ -864,7 +935,7 @@ __global__ void k_items(ItemArgs a) {
 
 constexpr int PB_THREADS = 256;
 constexpr int PB_WARPS = PB_THREADS / 32;
-constexpr int PB_SMEM_WORDS = 24576;  // 96 KB of staged P/D words
+constexpr int PB_SMEM_WORDS = PB_SMEM_WORDS_PLAN;  // 96 KB of staged words
 constexpr size_t PB_SMEM = PB_SMEM_WORDS * 4;
 constexpr int SCRATCH_SLOTS = 7;  // per-warp mask slots for wide anchors (>= max(R, 6))
 
@@ -889,9 +960,13 @@ struct Acc {
     unsigned long long tested = 0, leaves = 0, words = 0;
 };
 
+// binom(x, l) for x <= BINOM_TBL (shared memory; binom(256, 8) < 2^64)
+constexpr int BINOM_TBL = 256;
+
 // View of an anchor's candidate masks: P(w, c) and D(w, c).
 struct Masks {
     const uint32_t *base;
+    const unsigned long long *bt;  // binomial table
     uint32_t stride, W, nc;
     __device__ __forceinline__ uint32_t P(uint32_t w, uint32_t c) const {
         return base[(size_t)w * stride + c];
@@ -1252,8 +1327,12 @@ __device__ __forceinline__ void close_part(const Masks &m, const uint32_t (&y)[W
         if (w < (int)m.W) x1 += __popc(y[w] & m.D(w, c));
     acc.words += m.W;
     acc.leaves++;
-    binom_add(acc.sum, x1, l, err);
-    binom_add(acc.sum, n - x1, l, err);
+    if (n <= (uint32_t)BINOM_TBL) {
+        acc.sum.add(m.bt[x1] + m.bt[n - x1]);
+    } else {
+        binom_add(acc.sum, x1, l, err);
+        binom_add(acc.sum, n - x1, l, err);
+    }
 }
 
 template <int WN>
@@ -1386,8 +1465,12 @@ __device__ __forceinline__ void wide_close(const Masks &m, const uint32_t *part,
     acc.words += 2 * m.W;
     if ((int)n < l) return;
     acc.leaves++;
-    binom_add(acc.sum, x1, l, err);
-    binom_add(acc.sum, n - x1, l, err);
+    if (n <= (uint32_t)BINOM_TBL) {
+        acc.sum.add(m.bt[x1] + m.bt[n - x1]);
+    } else {
+        binom_add(acc.sum, x1, l, err);
+        binom_add(acc.sum, n - x1, l, err);
+    }
 }
 
 // Writes the parts of candidate i to scratch slots 0, 1; returns viability.
@@ -1477,6 +1560,86 @@ __device__ void wide_r3(const Masks &m, uint32_t *scratch, uint32_t wmax, uint32
     }
 }
 
+// ---- position side. For an anchor with few useful positions and many
+// candidates the same sum is taken over position subsets instead of
+// candidate subsets: expanding each binom(x, l) as the number of l-subsets Q
+// of a type class gives
+//   sum over R-subsets A, types k of binom(x[k], l)
+//     = sum over l-subsets Q of positions of binom(N_Q, R),
+// where N_Q counts the candidates w with Q inside the same-sign part
+// (P_w & ~D_w) or inside the different-sign part (P_w & D_w) of L[w] (the two
+// parts are disjoint, so w counts at most once). CM0[q] / CM1[q] are the
+// candidates whose same-sign / different-sign part holds position q; a warp
+// walks Q depth first with the candidate words spread over its lanes.
+
+template <int R>
+__device__ __forceinline__ void binom_add_r(U128 &acc, unsigned long long x, unsigned *err) {
+    if (x < (unsigned long long)R) return;
+    if constexpr (R == 1) {
+        acc.add(x);
+    } else {
+        if (x > c_binom64_max[R]) {
+            binom_add_slow(acc, x, R, err);
+            return;
+        }
+        acc.add(binom_u64<R>(x));
+    }
+}
+
+template <int R, int WPL, int LEV>
+__device__ void pos_expand(const uint32_t *cm, uint32_t dp, uint32_t wc, const uint32_t (&M0)[WPL],
+                           const uint32_t (&M1)[WPL], uint32_t start, int l, Acc &acc,
+                           unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    // q must leave room for the l - LEV positions still to choose after it
+    const int last = (int)dp - 1 - (l - LEV);
+    for (int qi = (int)start; qi <= last; qi++) {
+        const uint32_t q = (uint32_t)qi;
+        uint32_t X0[WPL], X1[WPL];
+        uint32_t n = 0;
+#pragma unroll
+        for (int k = 0; k < WPL; k++) {
+            const uint32_t w = lane + 32 * k;
+            X0[k] = w < wc ? (M0[k] & cm[(size_t)q * wc + w]) : 0u;
+            X1[k] = w < wc ? (M1[k] & cm[(size_t)(dp + q) * wc + w]) : 0u;
+            n += __popc(X0[k]) + __popc(X1[k]);
+        }
+        n = __reduce_add_sync(FULL, n);
+        if (lane == 0) {
+            acc.tested++;
+            acc.words += 2ull * wc;
+        }
+        if (n < (uint32_t)R) continue;
+        if (LEV == l) {
+            if (lane == 0) {
+                acc.leaves++;
+                binom_add_r<R>(acc.sum, n, err);
+            }
+        } else if constexpr (LEV < 8) {
+            pos_expand<R, WPL, LEV + 1>(cm, dp, wc, X0, X1, q + 1, l, acc, err);
+        }
+    }
+}
+
+// First position q1 of a position-side item.
+template <int R, int WPL>
+__device__ void pos_row(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q1, int l, Acc &acc,
+                        unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    uint32_t M0[WPL], M1[WPL];
+    uint32_t n = 0;
+#pragma unroll
+    for (int k = 0; k < WPL; k++) {
+        const uint32_t w = lane + 32 * k;
+        M0[k] = w < wc ? cm[(size_t)q1 * wc + w] : 0u;
+        M1[k] = w < wc ? cm[(size_t)(dp + q1) * wc + w] : 0u;
+        n += __popc(M0[k]) + __popc(M1[k]);
+    }
+    n = __reduce_add_sync(FULL, n);
+    if (n < (uint32_t)R) return;
+    pos_expand<R, WPL, 2>(cm, dp, wc, M0, M1, q1 + 1, l, acc, err);
+}
+
 template <int R>
 __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
@@ -1485,6 +1648,16 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
     __shared__ uint32_t s_rowpre[ROWS_MAX + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned *err = &a.cnt->err;
+    __shared__ unsigned long long s_binom[BINOM_TBL + 1];
+    for (int x = tid; x <= BINOM_TBL; x += PB_THREADS) {
+        unsigned long long v = 0;
+        if (x >= a.l) {
+            v = 1;
+            for (int i = 1; i <= a.l; i++) v = v * (unsigned long long)(x - a.l + i) / (unsigned long long)i;
+        }
+        s_binom[x] = v;
+    }
+    __syncthreads();
     uint32_t *scratch =
         a.wide_scratch ? a.wide_scratch + ((size_t)blockIdx.x * PB_WARPS + warp) * SCRATCH_SLOTS * a.wmax
                        : nullptr;
@@ -1499,7 +1672,41 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
         const uint32_t W = (a.dprime[r] + 31) / 32;
         const uint32_t rsv = a.rsv_c[r];
         const uint32_t *region = a.pool + a.pool_off[r];
+        Acc acc;
+        if (it.u1 == POS_ITEM) {
+            // position side: CM0 / CM1 (2 * dp rows of wc words) in shared memory
+            const uint32_t dp = a.dprime[r];
+            const uint32_t wc = (nc + 31) / 32;
+            for (uint32_t t = tid; t < 2 * dp * wc; t += PB_THREADS) sm[t] = 0;
+            if (tid == 0) s_unit = it.i0;
+            __syncthreads();
+            for (uint32_t c = tid; c < nc; c += PB_THREADS) {
+                const uint32_t cb = 1u << (c & 31), cw = c >> 5;
+                for (uint32_t w = 0; w < W; w++) {
+                    uint32_t pw = region[(size_t)w * rsv + c];
+                    const uint32_t dw = region[(size_t)(W + w) * rsv + c];
+                    while (pw) {
+                        const int b = __ffs(pw) - 1;
+                        pw &= pw - 1;
+                        const uint32_t q = 32 * w + b;
+                        const uint32_t part = (dw >> b) & 1u;
+                        atomicOr(&sm[(size_t)(part * dp + q) * wc + cw], cb);
+                    }
+                }
+            }
+            __syncthreads();
+            for (;;) {
+                uint32_t q1 = 0;
+                if (lane == 0) q1 = atomicAdd(&s_unit, 1u);
+                q1 = __shfl_sync(FULL, q1, 0);
+                if (q1 >= it.i1) break;
+                if (wc <= 32) pos_row<R, 1>(sm, dp, wc, q1, a.l, acc, err);
+                else if (wc <= 64) pos_row<R, 2>(sm, dp, wc, q1, a.l, acc, err);
+                else pos_row<R, 4>(sm, dp, wc, q1, a.l, acc, err);
+            }
+        } else {
         Masks m;
+        m.bt = s_binom;
         m.W = W;
         m.nc = nc;
         if (2ull * W * nc <= (unsigned long long)PB_SMEM_WORDS) {
@@ -1531,7 +1738,6 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
         }
         __syncthreads();
         const uint32_t total = s_total;
-        Acc acc;
         for (;;) {
             uint32_t u = 0;
             if (lane == 0) u = atomicAdd(&s_unit, 1u);
@@ -1576,7 +1782,8 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
                 else unit_wide<R>(m, scratch, a.wmax, i, jc, a.l, acc, err);
             }
         }
-        U128 ws = warp_sum_u128(acc.sum);
+        }
+                U128 ws = warp_sum_u128(acc.sum);
         if (lane == 0 && (ws.lo | ws.hi)) {
             atomic_add_u128(a.cnt->total, ws.lo, ws.hi);
             if (a.per_anchor) atomic_add_u128(a.per_anchor + 2 * (size_t)r, ws.lo, ws.hi);
@@ -1799,6 +2006,9 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     ia.dprime = dprime.ptr;
     ia.nX = nX;
     ia.R = R;
+    ia.l = l;
+    ia.method = (opts && (opts->flags & SBC_COUNT_CANDIDATE_SIDE)) ? 1
+              : (opts && (opts->flags & SBC_COUNT_POSITION_SIDE)) ? 2 : 0;
     ia.cnt = cnt.ptr;
     ia.item_cost = 0;
     ia.item_off = nullptr;

@@ -262,3 +262,33 @@ def test_sharding_partitions_anchors(sbc, small):
     with sbc.graph_from_synth(small) as h:
         parts = [sbc.sbc_count_ex(h, 3, 3, shard=i, shard_count=3)[0] for i in range(3)]
     assert sum(parts) == want
+
+
+# ---------------------------------------------------------------- both sides
+
+@pytest.mark.parametrize("method", ["candidate", "position"])
+@pytest.mark.parametrize("seed", range(3))
+def test_enumeration_sides_agree(sbc, method, seed):
+    """Candidate-subset and position-subset enumeration give the oracle's
+    count (totals and per anchor) on random graphs and all (p,q) in [2,5]^2."""
+    rng = random.Random(seed)
+    g = sbc_synth.chung_lu_signed(500 + seed, rng.randint(200, 900), rng.randint(200, 900),
+                                  rng.randint(2000, 9000), 2.0, 2.2, 0.15)
+    with sbc.graph_from_synth(g) as h:
+        for p in range(2, 6):
+            for q in range(2, 6):
+                want, per = oracle.count(g, p, q, side=0, per_anchor=True)
+                got, st, pa = sbc.sbc_count_ex(h, p, q, anchor_side=0, method=method,
+                                               per_anchor=True)
+                assert got == want, (p, q, method)
+                assert pa == per, (p, q, method)
+
+
+@pytest.mark.parametrize("method", ["auto", "candidate", "position"])
+def test_small_workload_all_methods(sbc, small, method):
+    with sbc.graph_from_synth(small) as h:
+        for p, q in [(3, 3), (4, 4), (3, 4), (4, 3)]:
+            want = oracle.count(small, p, q, side=0)
+            for side in (0, 1):
+                got, _, _ = sbc.sbc_count_ex(h, p, q, anchor_side=side, method=method)
+                assert got == want, (p, q, side, method)
