@@ -49,6 +49,7 @@ extern "C" {
 
 typedef struct sbc_graph sbc_graph;   /* opaque, immutable after creation */
 typedef struct sbc_server sbc_server; /* opaque request server */
+typedef struct sbc_batch sbc_batch;   /* opaque planned batch of graphs */
 
 /* Unsigned 128-bit integer, little-endian limbs: value = lo + hi * 2^64. */
 typedef struct {
@@ -176,6 +177,32 @@ sbc_status sbc_count_ex(const sbc_graph *g, int p, int q, const sbc_count_opts *
 sbc_status sbc_count_csr(int64_t n_u, int64_t n_v, int64_t nnz, const void *row_offsets,
                          const int32_t *cols, const void *signs, uint32_t flags, int p, int q,
                          sbc_u128 *out, void *stream);
+
+/*
+ * Batched counting. A batch of independent graphs is counted as their
+ * disjoint union: a biclique is connected, so each balanced (p,q)-biclique
+ * lies in one graph (Section 3's definitions), and one pass of the counting
+ * kernels over the union (Algorithm 2 per graph, each graph on its preferred
+ * anchor side) yields every graph's count. The graphs must be on the current
+ * device; they are only read.
+ *
+ * sbc_count_batch: count the n graphs once; out[i] = count of graphs[i]
+ * (p from U, q from V). Synchronises `stream`.
+ */
+sbc_status sbc_count_batch(const sbc_graph *const *graphs, size_t n, int p, int q, sbc_u128 *out,
+                           void *stream);
+
+/*
+ * A planned batch for repeated counts of the same resident graphs: creation
+ * plans the union and counts it once; sbc_batch_run re-executes the counting
+ * kernels (2-hop and tuple kernels of every graph) from a CUDA graph captured
+ * at creation and writes out[i] for each graph. The graphs must outlive the
+ * batch and stay unchanged. Runs on one batch must not overlap.
+ */
+sbc_status sbc_batch_create(const sbc_graph *const *graphs, size_t n, int p, int q,
+                            sbc_batch **out, void *stream);
+sbc_status sbc_batch_run(sbc_batch *b, sbc_u128 *out, void *stream);
+sbc_status sbc_batch_destroy(sbc_batch *b);
 
 /*
  * sbc_count_csr without any device allocation, for callers that cannot call

@@ -20,7 +20,7 @@ from . import build as _build
 __all__ = [
     "SbcError", "Graph", "sbc_graph_create", "sbc_graph_destroy", "sbc_graph_info",
     "sbc_count", "sbc_count_ex", "sbc_count_csr", "sbc_last_error", "sbc_version",
-    "sbc_launch_count", "sbc_count_csr_noalloc",
+    "sbc_launch_count", "sbc_count_csr_noalloc", "sbc_count_batch", "Batch",
     "lib", "LIB_PATH",
 ]
 
@@ -110,6 +110,12 @@ _declare("sbc_count_csr", ctypes.c_int,
 _declare("sbc_last_error", ctypes.c_char_p, [])
 _declare("sbc_version", ctypes.c_char_p, [])
 _declare("sbc_launch_count", ctypes.c_uint64, [])
+_declare("sbc_count_batch", ctypes.c_int,
+         [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(U128), _vp])
+_declare("sbc_batch_create", ctypes.c_int,
+         [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp), _vp])
+_declare("sbc_batch_run", ctypes.c_int, [_vp, ctypes.POINTER(U128), _vp])
+_declare("sbc_batch_destroy", ctypes.c_int, [_vp])
 _declare("sbc_count_csr_noalloc", ctypes.c_int,
          [_i64, _i64, _i64, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
           ctypes.POINTER(U128), _vp])
@@ -308,6 +314,56 @@ def sbc_count_csr_noalloc(n_u: int, n_v: int, row_offsets, cols, signs, p: int, 
     _check(lib.sbc_count_csr_noalloc(n_u, n_v, int(cols.shape[0]), off_p, col_p, sg_p, flags, p,
                                      q, ctypes.byref(out), _stream_ptr(stream)))
     return out.value()
+
+
+def _handles(graphs):
+    arr = (_vp * max(len(graphs), 1))()
+    for i, g in enumerate(graphs):
+        arr[i] = g.handle
+    return arr
+
+
+def sbc_count_batch(graphs, p: int, q: int, stream=None) -> list:
+    """sbc_count_batch: one pass of the counting kernels over a batch of
+    resident graphs; returns each graph's exact count."""
+    out = (U128 * max(len(graphs), 1))()
+    _check(lib.sbc_count_batch(_handles(graphs), len(graphs), p, q, out, _stream_ptr(stream)))
+    return [out[i].value() for i in range(len(graphs))]
+
+
+class Batch:
+    """A planned batch (sbc_batch_create); run() replays its counting kernels
+    from a captured CUDA graph."""
+
+    def __init__(self, graphs, p: int, q: int, stream=None):
+        self.graphs = list(graphs)  # keep the graphs alive
+        h = _vp()
+        _check(lib.sbc_batch_create(_handles(self.graphs), len(self.graphs), p, q, ctypes.byref(h),
+                                    _stream_ptr(stream)))
+        self.handle = h.value
+
+    def run(self, stream=None) -> list:
+        n = len(self.graphs)
+        out = (U128 * max(n, 1))()
+        _check(lib.sbc_batch_run(self.handle, out, _stream_ptr(stream)))
+        return [out[i].value() for i in range(n)]
+
+    def close(self):
+        if self.handle:
+            _check(lib.sbc_batch_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def graph_from_synth(g, device: bool = False, sign_bits: bool = False, stream=None) -> Graph:

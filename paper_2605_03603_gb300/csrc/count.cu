@@ -40,25 +40,30 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 
 // ------------------------------------------------------------------ counters
 
-// Device-side scalars of one count.
+// Device-side scalars of one count. Fields up to `run_begin` are set while
+// planning (they stay valid when the counting kernels are replayed); the
+// rest are accumulators and queue heads of one execution.
 struct Counters {
-    unsigned long long total[2];       // u128 count
     unsigned long long tuples_paper[2];// u128, sum binom(|C_paper|, R)
     unsigned long long tuples_ours[2]; // u128, sum binom(|C'|, R)
     unsigned long long candidates;     // sum |C'| (or |C_paper| in stats mode)
-    unsigned long long wedges;         // 2-hop entries visited
     unsigned long long cost_total;     // tuple-phase cost estimate
+    unsigned long long e_max;          // largest visited-wedge count of a large anchor
+    unsigned int n_active;             // anchors with work
+    unsigned int n_big;                // anchors for the CTA-wide 2-hop kernel
+    unsigned int n_items;
+    unsigned int plan_pad;
+    // ---- per execution
+    unsigned long long run_begin;      // marker (unused)
+    unsigned long long total[2];       // u128 count
+    unsigned long long wedges;         // 2-hop entries visited
     unsigned long long tested;         // tuples whose common-neighbour mask was tested
     unsigned long long leaves;         // tuples with |T| >= l (type counts taken)
     unsigned long long popc_words;     // mask words popcounted: W per test, 2^R W per leaf
-    unsigned int n_active;             // anchors with work
-    unsigned int n_big;                // anchors for the CTA-wide 2-hop kernel
     unsigned int head_large;           // 2-hop queue heads
     unsigned int head_small;
     unsigned int head_b;               // tuple queue head
-    unsigned int n_items;
     unsigned int err;                  // error bits
-    unsigned int pad;
 };
 
 enum : unsigned {
@@ -218,7 +223,10 @@ __global__ void k_plan(const int64_t *__restrict__ A_off, const uint32_t *__rest
                              : 0xFFFFFFFFu;
             sval[r] = (uint32_t)r;
             if (active) atomicAdd(&cnt->n_active, 1u);
-            if (active && cost > (unsigned long long)small_e) atomicAdd(&cnt->n_big, 1u);
+            if (active && cost > (unsigned long long)small_e) {
+                atomicAdd(&cnt->n_big, 1u);
+                atomicMax(&cnt->e_max, cost);
+            }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) rsv_w[nX] = 0;
@@ -305,6 +313,8 @@ struct TwohopArgs {
     uint32_t *pool;
     uint32_t *ncand, *npaper;
     Counters *cnt;
+    unsigned long long *bucket;     // per-CTA bucket slots of the large-anchor kernel
+    unsigned long long bucket_slot; // entries per slot
     int l;
 };
 
@@ -461,7 +471,9 @@ __global__ void __launch_bounds__(PS_THREADS) k_twohop_small(TwohopArgs a) {
 constexpr int PL_THREADS = 512;
 constexpr int PL_WARPS = PL_THREADS / 32;
 constexpr int PL_HS = 7168;             // slots
-constexpr int PL_WCAP = PL_HS / 2;      // visited wedges per window (load <= 1/2)
+constexpr int PL_WCAP = PL_HS / 2;      // visited wedges per re-read window (load <= 1/2)
+constexpr int PL_BCAP = PL_HS / 3;      // expected entries per bucket (bucket <= 1.5x + 64)
+constexpr int PL_MAXCLS = 1024;         // bucket classes per anchor
 constexpr int PL_PCH = PL_THREADS;      // positions staged per chunk
 constexpr int PL_STAGE_WORDS = 4096;    // staged P/D words
 constexpr size_t PL_OFF_VALS = (size_t)PL_HS * 4;
@@ -471,24 +483,40 @@ constexpr size_t PL_OFF_PINFO = PL_OFF_PPRE + (size_t)(PL_PCH + 4) * 4;
 constexpr size_t PL_OFF_STAGE = PL_OFF_PINFO + (size_t)PL_PCH * 4;
 constexpr size_t PL_SMEM = PL_OFF_STAGE + (size_t)PL_STAGE_WORDS * 4;
 
-__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *warp_tot,
-                                                        uint32_t *total) {
+// Bucket entry of a wedge: w (bits 0..30), sdiff (bit 31), bit index of the
+// position (bits 32..52; all ones when the position is not useful).
+constexpr unsigned long long BE_NOBIT = (1ull << 21) - 1;
+
+__host__ __device__ __forceinline__ unsigned long long bucket_cap(unsigned long long e_vis, int lg) {
+    return ((e_vis >> lg) * 3) / 2 + 65;
+}
+
+// Largest bucket area one anchor can need: sum of its classes' capacities.
+__host__ __device__ __forceinline__ int bucket_lg(unsigned long long e_vis) {
+    int lg = 0;
+    while (((unsigned long long)PL_BCAP << lg) < e_vis && lg < 10) lg++;
+    return lg;
+}
+
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long v,
+                                                                  unsigned long long *warp_tot,
+                                                                  unsigned long long *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = PL_WARPS;
-    uint32_t incl = v;
+    unsigned long long incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(FULL, incl, o);
+        unsigned long long t = __shfl_up_sync(FULL, incl, o);
         if (lane >= o) incl += t;
     }
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        uint32_t wv = lane < NW ? warp_tot[lane] : 0u;
-        uint32_t wi = wv;
+        unsigned long long wv = lane < NW ? warp_tot[lane] : 0ull;
+        unsigned long long wi = wv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(FULL, wi, o);
+            unsigned long long t = __shfl_up_sync(FULL, wi, o);
             if (lane >= o) wi += t;
         }
         if (lane < NW) warp_tot[lane] = wi - wv;
@@ -498,45 +526,66 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *wa
     return warp_tot[warp] + incl - v;
 }
 
-// Visit the anchor's 2-hop entries of hash class `cls` with the whole CTA.
-// Positions are staged PL_PCH at a time; each thread takes every PL_THREADS-th
-// entry of the chunk's flattened suffixes. fn(w, sdiff, bit).
+// Visit the anchor's 2-hop entries with the whole CTA; with lg_nw > 0 only
+// entries of hash class `cls`. Positions are staged PL_PCH at a time and the
+// non-empty ones compacted; each warp takes 32 consecutive entries, one
+// binary search for the first and short forward walks for the others.
+// fn(w, sdiff, bit).
 template <typename F>
 __device__ __forceinline__ void visit_block(int64_t ebase, int d, bool useful_only, int lg_nw,
                                             uint32_t cls, const TwohopArgs &a, int64_t *pst,
-                                            uint32_t *ppre, uint32_t *pinfo, uint32_t *warp_tot,
-                                            uint32_t *s_total, F fn) {
-    const int tid = threadIdx.x;
+                                            uint32_t *ppre, uint32_t *pinfo,
+                                            unsigned long long *warp_tot,
+                                            unsigned long long *s_total, F fn) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int c0 = 0; c0 < d; c0 += PL_PCH) {
         const int nch = d - c0 < PL_PCH ? d - c0 : PL_PCH;
-        uint32_t len = 0;
+        uint32_t len = 0, info = 0;
+        int64_t st = 0;
         if (tid < nch) {
             int64_t e = ebase + c0 + tid;
             uint32_t av = a.A_ent[e];
             uint32_t y = av & VMASK;
             uint32_t bit = a.A_bit[e];
-            int64_t st = a.B_off[y] + (int64_t)a.A_pos[e] + 1;
+            st = a.B_off[y] + (int64_t)a.A_pos[e] + 1;
             len = (uint32_t)(a.B_off[y + 1] - st);
             if (useful_only && bit == EMPTY) len = 0;
-            pst[tid] = st;
-            pinfo[tid] = (av & 0x80000000u) | (bit == EMPTY ? NOBIT : bit);
+            info = (av & 0x80000000u) | (bit == EMPTY ? NOBIT : bit);
         }
-        uint32_t ex = block_excl_scan_u32(len, warp_tot, s_total);
-        ppre[tid] = ex;
+        // scan of (non-empty flag, length): compact slot and entry prefix
+        unsigned long long packed = len ? ((1ull << 32) | len) : 0ull;
+        unsigned long long ex = block_excl_scan_u64(packed, warp_tot, s_total);
+        if (len) {
+            const uint32_t slot = (uint32_t)(ex >> 32);
+            pst[slot] = st;
+            pinfo[slot] = info;
+            ppre[slot] = (uint32_t)ex;
+        }
         __syncthreads();
-        const uint32_t total = *s_total;
-        for (uint32_t t = tid; t < total; t += PL_THREADS) {
-            uint32_t lo = 0, hi = (uint32_t)nch;  // largest j with ppre[j] <= t
-            while (hi - lo > 1) {
-                uint32_t mid = (lo + hi) >> 1;
-                if (ppre[mid] <= t) lo = mid; else hi = mid;
+        const uint32_t npos = (uint32_t)(*s_total >> 32);
+        const uint32_t total = (uint32_t)*s_total;
+        for (uint32_t base = (uint32_t)warp * 32; base < total; base += PL_THREADS) {
+            uint32_t p0 = 0;
+            if (lane == 0) {
+                uint32_t lo = 0, hi = npos;  // largest j with ppre[j] <= base
+                while (hi - lo > 1) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if (ppre[mid] <= base) lo = mid; else hi = mid;
+                }
+                p0 = lo;
             }
-            uint32_t ent = a.B_ent[pst[lo] + (t - ppre[lo])];
-            uint32_t w = ent & VMASK;
-            if (class_of(w, lg_nw) != cls) continue;
-            uint32_t info = pinfo[lo];
-            uint32_t bit = info & NOBIT;
-            fn(w, (info >> 31) ^ (ent >> 31), bit == NOBIT ? EMPTY : bit);
+            uint32_t p = __shfl_sync(FULL, p0, 0);
+            const uint32_t t = base + lane;
+            if (t < total) {
+                while (p + 1 < npos && ppre[p + 1] <= t) p++;
+                uint32_t ent = a.B_ent[pst[p] + (t - ppre[p])];
+                uint32_t w = ent & VMASK;
+                if (lg_nw == 0 || class_of(w, lg_nw) == cls) {
+                    uint32_t inf = pinfo[p];
+                    uint32_t bit = inf & NOBIT;
+                    fn(w, (inf >> 31) ^ (ent >> 31), bit == NOBIT ? EMPTY : bit);
+                }
+            }
         }
         __syncthreads();
     }
@@ -551,13 +600,49 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
     uint32_t *ppre = (uint32_t *)(smem_raw + PL_OFF_PPRE);
     uint32_t *pinfo = (uint32_t *)(smem_raw + PL_OFF_PINFO);
     uint32_t *stage = (uint32_t *)(smem_raw + PL_OFF_STAGE);
-    __shared__ uint32_t warp_tot[PL_WARPS];
-    __shared__ uint32_t s_total;
+    __shared__ unsigned long long warp_tot[PL_WARPS];
+    __shared__ unsigned long long s_total;
     __shared__ unsigned s_item, s_ncw, s_paper, s_ovf;
+    __shared__ uint32_t s_bcnt[PL_MAXCLS];
     const int tid = threadIdx.x, lane = tid & 31;
     const int l = a.l;
     const unsigned n_big = a.cnt->n_big;
+    unsigned long long *bucket =
+        a.bucket ? a.bucket + (size_t)blockIdx.x * a.bucket_slot : nullptr;
     unsigned long long wedges = 0;
+
+    // Candidate filter over the table, window-local indices in vals.
+    auto extract = [&](uint32_t hs) {
+        for (uint32_t base = 0; base < hs; base += PL_THREADS) {
+            uint32_t i = base + tid;
+            bool cand = false, pap = false;
+            if (i < hs && keys[i] != EMPTY) {
+                unsigned long long v = vals[i];
+                pap = STATS && (v & M21) >= (unsigned long long)l;
+                cand = keep_candidate(v, l);
+            }
+            uint32_t bal = __ballot_sync(FULL, cand);
+            uint32_t pb = __ballot_sync(FULL, pap);
+            uint32_t wbase = 0;
+            if (lane == 0 && bal) wbase = atomicAdd(&s_ncw, (unsigned)__popc(bal));
+            if (lane == 0 && pb) atomicAdd(&s_paper, (unsigned)__popc(pb));
+            wbase = __shfl_sync(FULL, wbase, 0);
+            if (cand) vals[i] = CAND | (wbase + __popc(bal & ((1u << lane) - 1u)));
+        }
+    };
+    auto set_bits = [&](uint32_t hs, uint32_t *bb, uint32_t bstride, uint32_t W, uint32_t w,
+                        uint32_t sdiff, uint32_t bit) {
+        int sl = tab_find(keys, hs, w);
+        if (sl < 0) return;
+        unsigned long long v = vals[sl];
+        if (!(v & CAND)) return;
+        uint32_t c = (uint32_t)v;
+        uint32_t m = 1u << (bit & 31);
+        size_t wd = bit >> 5;
+        atomicOr(&bb[wd * bstride + c], m);
+        if (sdiff) atomicOr(&bb[(W + wd) * bstride + c], m);
+    };
+
     for (;;) {
         if (tid == 0) s_item = atomicAdd(&a.cnt->head_large, 1u);
         __syncthreads();
@@ -571,100 +656,176 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
         const uint32_t rsv = a.rsv_c[r];
         uint32_t *region = a.pool + a.pool_off[r];
         const unsigned long long e_vis = STATS ? a.e_all[r] : a.e_use[r];
-        int lg_nw = 0;
-        while (((unsigned long long)PL_WCAP << lg_nw) < e_vis) lg_nw++;
         uint32_t nc = 0, npaper = 0;
         bool failed = false;
-        for (int attempt = 0; attempt < 8; attempt++) {
-            const uint32_t nw = 1u << lg_nw;
-            const unsigned long long per = (e_vis + nw - 1) >> lg_nw;
-            uint32_t hs = (uint32_t)((2 * per + 31) & ~31ull);
-            hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
-            nc = 0;
-            npaper = 0;
-            bool restart = false;
-            for (uint32_t cls = 0; cls < nw && !failed; cls++) {
-                for (uint32_t i = tid; i < hs; i += PL_THREADS) {
-                    keys[i] = EMPTY;
-                    vals[i] = 0;
+
+        // Window bookkeeping shared by both strategies: after the table of
+        // one window holds its counts, keep candidates and write their bits.
+        // Returns false when the reservation would overflow.
+        auto finish_window = [&](uint32_t hs, auto &&pass2) -> bool {
+            extract(hs);
+            __syncthreads();
+            const uint32_t ncw = s_ncw;
+            npaper += s_paper;
+            if (ncw > 0) {
+                if (nc + ncw > rsv) {
+                    if (tid == 0) atomicOr(&a.cnt->err, CERR_RESERVE);
+                    __syncthreads();
+                    return false;
                 }
-                if (tid == 0) {
-                    s_ncw = 0;
-                    s_paper = 0;
-                    s_ovf = 0;
-                }
-                __syncthreads();
-                visit_block(ebase, d, !STATS, lg_nw, cls, a, pst, ppre, pinfo, warp_tot, &s_total,
-                            [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
-                                if (!tab_insert(keys, vals, hs, w, pass1_add(sdiff, bit))) s_ovf = 1;
-                            });
-                if (s_ovf) {
-                    restart = true;
-                    break;
-                }
-                for (uint32_t base = 0; base < hs; base += PL_THREADS) {
-                    uint32_t i = base + tid;
-                    bool cand = false, pap = false;
-                    if (i < hs && keys[i] != EMPTY) {
-                        unsigned long long v = vals[i];
-                        pap = STATS && (v & M21) >= (unsigned long long)l;
-                        cand = keep_candidate(v, l);
-                    }
-                    uint32_t bal = __ballot_sync(FULL, cand);
-                    uint32_t pb = __ballot_sync(FULL, pap);
-                    uint32_t wbase = 0;
-                    if (lane == 0 && bal) wbase = atomicAdd(&s_ncw, (unsigned)__popc(bal));
-                    if (lane == 0 && pb) atomicAdd(&s_paper, (unsigned)__popc(pb));
-                    wbase = __shfl_sync(FULL, wbase, 0);
-                    if (cand) vals[i] = CAND | (wbase + __popc(bal & ((1u << lane) - 1u)));
+                const bool staged = 2ull * W * ncw <= (unsigned long long)PL_STAGE_WORDS;
+                uint32_t *bb = staged ? stage : region + nc;
+                const uint32_t bstride = staged ? ncw : rsv;
+                for (uint32_t i = tid; i < 2 * W * ncw; i += PL_THREADS) {
+                    uint32_t wd = i / ncw, c = i % ncw;
+                    bb[(size_t)wd * bstride + c] = 0;
                 }
                 __syncthreads();
-                const uint32_t ncw = s_ncw;
-                npaper += s_paper;
-                if (ncw > 0) {
-                    if (nc + ncw > rsv) {
-                        if (tid == 0) atomicOr(&a.cnt->err, CERR_RESERVE);
-                        failed = true;
-                        __syncthreads();
-                        break;
-                    }
-                    const bool staged = 2ull * W * ncw <= (unsigned long long)PL_STAGE_WORDS;
-                    uint32_t *bb = staged ? stage : region + nc;
-                    const uint32_t bstride = staged ? ncw : rsv;
+                pass2(bb, bstride);
+                __syncthreads();
+                if (staged) {
                     for (uint32_t i = tid; i < 2 * W * ncw; i += PL_THREADS) {
                         uint32_t wd = i / ncw, c = i % ncw;
-                        bb[(size_t)wd * bstride + c] = 0;
+                        region[(size_t)wd * rsv + nc + c] = stage[i];
+                    }
+                }
+                nc += ncw;
+            }
+            __syncthreads();
+            return true;
+        };
+        auto clear_table = [&](uint32_t hs) {
+            for (uint32_t i = tid; i < hs; i += PL_THREADS) {
+                keys[i] = EMPTY;
+                vals[i] = 0;
+            }
+            if (tid == 0) {
+                s_ncw = 0;
+                s_paper = 0;
+                s_ovf = 0;
+            }
+            __syncthreads();
+        };
+
+        const int lgb = bucket_lg(e_vis);
+        bool bucketed = false;
+        if (e_vis <= (unsigned long long)PL_WCAP) {
+            // one window
+            uint32_t hs = (uint32_t)((2 * e_vis + 31) & ~31ull);
+            hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
+            clear_table(hs);
+            visit_block(ebase, d, !STATS, 0, 0, a, pst, ppre, pinfo, warp_tot, &s_total,
+                        [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                            if (!tab_insert(keys, vals, hs, w, pass1_add(sdiff, bit))) s_ovf = 1;
+                        });
+            if (s_ovf) {
+                failed = true;
+                if (tid == 0) atomicOr(&a.cnt->err, CERR_HASH);
+            } else {
+                failed = !finish_window(hs, [&](uint32_t *bb, uint32_t bstride) {
+                    visit_block(ebase, d, true, 0, 0, a, pst, ppre, pinfo, warp_tot, &s_total,
+                                [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                                    set_bits(hs, bb, bstride, W, w, sdiff, bit);
+                                });
+                });
+            }
+        } else if (bucket && lgb <= 10 &&
+                   (bucket_cap(e_vis, lgb) << lgb) <= a.bucket_slot) {
+            // partition the wedges once into 2^lgb hash classes, then one
+            // window per class from its bucket
+            const uint32_t ncls = 1u << lgb;
+            const uint32_t cap = (uint32_t)bucket_cap(e_vis, lgb);
+            for (uint32_t i = tid; i < ncls; i += PL_THREADS) s_bcnt[i] = 0;
+            if (tid == 0) s_ovf = 0;
+            __syncthreads();
+            visit_block(ebase, d, !STATS, 0, 0, a, pst, ppre, pinfo, warp_tot, &s_total,
+                        [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                            uint32_t c = class_of(w, lgb);
+                            uint32_t pos = atomicAdd(&s_bcnt[c], 1u);
+                            if (pos < cap) {
+                                unsigned long long bi = bit == EMPTY ? BE_NOBIT : (unsigned long long)bit;
+                                bucket[(size_t)c * cap + pos] =
+                                    (unsigned long long)w | ((unsigned long long)sdiff << 31) | (bi << 32);
+                            } else {
+                                s_ovf = 1;
+                            }
+                        });
+            bucketed = !s_ovf;
+            __syncthreads();
+            if (bucketed) {
+                for (uint32_t c = 0; c < ncls && !failed; c++) {
+                    const uint32_t n = s_bcnt[c];
+                    const unsigned long long *bk = bucket + (size_t)c * cap;
+                    uint32_t hs = (uint32_t)((2ull * n + 31) & ~31ull);
+                    hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
+                    __syncthreads();
+                    clear_table(hs);
+                    for (uint32_t i = tid; i < n; i += PL_THREADS) {
+                        unsigned long long e = bk[i];
+                        uint32_t bi = (uint32_t)(e >> 32);
+                        uint32_t bit = bi == (uint32_t)BE_NOBIT ? EMPTY : bi;
+                        if (!tab_insert(keys, vals, hs, (uint32_t)e & VMASK,
+                                        pass1_add((uint32_t)(e >> 31) & 1u, bit)))
+                            s_ovf = 1;
                     }
                     __syncthreads();
-                    visit_block(ebase, d, true, lg_nw, cls, a, pst, ppre, pinfo, warp_tot, &s_total,
-                                [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
-                                    int sl = tab_find(keys, hs, w);
-                                    if (sl < 0) return;
-                                    unsigned long long v = vals[sl];
-                                    if (!(v & CAND)) return;
-                                    uint32_t c = (uint32_t)v;
-                                    uint32_t m = 1u << (bit & 31);
-                                    size_t wd = bit >> 5;
-                                    atomicOr(&bb[wd * bstride + c], m);
-                                    if (sdiff) atomicOr(&bb[(W + wd) * bstride + c], m);
-                                });
-                    if (staged) {
-                        for (uint32_t i = tid; i < 2 * W * ncw; i += PL_THREADS) {
-                            uint32_t wd = i / ncw, c = i % ncw;
-                            region[(size_t)wd * rsv + nc + c] = stage[i];
-                        }
+                    if (s_ovf) {
+                        failed = true;
+                        if (tid == 0) atomicOr(&a.cnt->err, CERR_HASH);
+                        break;
                     }
-                    nc += ncw;
+                    failed = !finish_window(hs, [&](uint32_t *bb, uint32_t bstride) {
+                        for (uint32_t i = tid; i < n; i += PL_THREADS) {
+                            unsigned long long e = bk[i];
+                            uint32_t bi = (uint32_t)(e >> 32);
+                            if (bi == (uint32_t)BE_NOBIT) continue;
+                            set_bits(hs, bb, bstride, W, (uint32_t)e & VMASK,
+                                     (uint32_t)(e >> 31) & 1u, bi);
+                        }
+                    });
+                }
+            }
+        }
+        if (!bucketed && !failed && e_vis > (unsigned long long)PL_WCAP) {
+            // re-read windows: every pass over the 2-hop keeps one hash class
+            nc = 0;
+            npaper = 0;
+            int lg_nw = 0;
+            while (((unsigned long long)PL_WCAP << lg_nw) < e_vis) lg_nw++;
+            for (int attempt = 0; attempt < 8 && !failed; attempt++) {
+                const uint32_t nw = 1u << lg_nw;
+                const unsigned long long per = (e_vis + nw - 1) >> lg_nw;
+                uint32_t hs = (uint32_t)((2 * per + 31) & ~31ull);
+                hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
+                nc = 0;
+                npaper = 0;
+                bool restart = false;
+                for (uint32_t cls = 0; cls < nw && !failed; cls++) {
+                    clear_table(hs);
+                    visit_block(ebase, d, !STATS, lg_nw, cls, a, pst, ppre, pinfo, warp_tot,
+                                &s_total, [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                                    if (!tab_insert(keys, vals, hs, w, pass1_add(sdiff, bit)))
+                                        s_ovf = 1;
+                                });
+                    if (s_ovf) {
+                        restart = true;
+                        break;
+                    }
+                    failed = !finish_window(hs, [&](uint32_t *bb, uint32_t bstride) {
+                        visit_block(ebase, d, true, lg_nw, cls, a, pst, ppre, pinfo, warp_tot,
+                                    &s_total, [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                                        set_bits(hs, bb, bstride, W, w, sdiff, bit);
+                                    });
+                    });
+                }
+                if (!restart) break;
+                lg_nw++;
+                if (attempt == 7) {
+                    if (tid == 0) atomicOr(&a.cnt->err, CERR_HASH);
+                    failed = true;
                 }
                 __syncthreads();
             }
-            if (!restart || failed) break;
-            lg_nw++;
-            if (attempt == 7) {
-                if (tid == 0) atomicOr(&a.cnt->err, CERR_HASH);
-                failed = true;
-            }
-            __syncthreads();
         }
         if (failed) nc = 0;
         if (tid == 0) {
@@ -701,13 +862,14 @@ constexpr uint32_t POS_ITEM = 0xFFFFFFFFu;
 constexpr int POS_MAX_WORDS = 128;  // candidate words of a position-side mask (4 per lane)
 
 constexpr int ROWS_MAX = 1024;
-constexpr int PB_SMEM_WORDS_PLAN = 24576;  // staged words of the tuple kernel (PB_SMEM_WORDS)
+constexpr int PB_SMEM_WORDS_PLAN = 16384;  // staged words of the tuple kernel (PB_SMEM_WORDS)
 
 struct ItemArgs {
     const uint32_t *ncand, *npaper, *dprime;
     int64_t nX;
     int R, l;
     int method;  // 0: cheaper side per anchor, 1: candidate side, 2: position side where it fits
+    unsigned long long pos_unit;  // cost of one position-side prefix node per candidate word-lane
     unsigned long long item_cost;
     const int64_t *item_off;  // emit pass
     int64_t *item_cnt;        // count pass (nX + 1 entries)
@@ -748,26 +910,27 @@ __device__ __forceinline__ bool pos_fits(uint32_t nc, uint32_t dp, int l) {
 }
 
 __device__ __forceinline__ unsigned long long pos_row_cost(uint32_t nc, uint32_t dp, uint32_t q1,
-                                                           int l) {
+                                                           int l, unsigned long long unit) {
     const unsigned long long wpl = ((nc + 31) / 32 + 31) / 32;
     unsigned long long nodes = 0;
     for (int i = 0; i < l; i++) {
         unsigned long long t = binom_sat(dp - 1 - q1, i);
         nodes = (nodes + t < nodes) ? 0xFFFFFFFFFFFFFFFFull : nodes + t;
     }
-    unsigned long long c = nodes * 96ull * wpl;
-    return (c / (96ull * wpl) != nodes) ? 0xFFFFFFFFFFFFFFFFull : c;
+    unsigned long long c = nodes * unit * wpl;
+    return (c / (unit * wpl) != nodes) ? 0xFFFFFFFFFFFFFFFFull : c;
 }
 
-__device__ __forceinline__ unsigned long long pos_cost(uint32_t nc, uint32_t dp, int l) {
+__device__ __forceinline__ unsigned long long pos_cost(uint32_t nc, uint32_t dp, int l,
+                                                       unsigned long long unit) {
     const unsigned long long wpl = ((nc + 31) / 32 + 31) / 32;
     unsigned long long nodes = 0;
     for (int i = 1; i <= l; i++) {
         unsigned long long t = binom_sat(dp, i);
         nodes = (nodes + t < nodes) ? 0xFFFFFFFFFFFFFFFFull : nodes + t;
     }
-    unsigned long long c = nodes * 96ull * wpl;
-    return (c / (96ull * wpl) != nodes) ? 0xFFFFFFFFFFFFFFFFull : c;
+    unsigned long long c = nodes * unit * wpl;
+    return (c / (unit * wpl) != nodes) ? 0xFFFFFFFFFFFFFFFFull : c;
 }
 
 __device__ __forceinline__ unsigned long long cand_cost(uint32_t nc, uint32_t W, int R) {
@@ -777,10 +940,11 @@ __device__ __forceinline__ unsigned long long cand_cost(uint32_t nc, uint32_t W,
 }
 
 // True when the anchor takes the position side (cheaper, or forced).
-__device__ __forceinline__ bool use_pos(uint32_t nc, uint32_t dp, int R, int l, int method) {
+__device__ __forceinline__ bool use_pos(uint32_t nc, uint32_t dp, int R, int l, int method,
+                                        unsigned long long unit) {
     if (method == 1 || nc < (uint32_t)R || !pos_fits(nc, dp, l)) return false;
     if (method == 2) return true;
-    return pos_cost(nc, dp, l) < cand_cost(nc, (dp + 31) / 32, R);
+    return pos_cost(nc, dp, l, unit) < cand_cost(nc, (dp + 31) / 32, R);
 }
 
 // Anchor cost, anchor tuple counts. Thread per anchor.
@@ -815,7 +979,7 @@ __global__ void k_anchor_cost(ItemArgs a) {
         if (nc >= (uint32_t)a.R) {
             unsigned long long t = binom_sat(nc, a.R);
             to.add(t);
-            unsigned long long c = use_pos(nc, a.dprime[r], a.R, a.l, a.method) ? pos_cost(nc, a.dprime[r], a.l)
+            unsigned long long c = use_pos(nc, a.dprime[r], a.R, a.l, a.method, a.pos_unit) ? pos_cost(nc, a.dprime[r], a.l, a.pos_unit)
                                                                      : cand_cost(nc, W, a.R);
             cost = (cost + c < cost) ? 0xFFFFFFFFFFFFFFFFull : cost + c;
         }
@@ -862,13 +1026,13 @@ __global__ void k_items(ItemArgs a) {
             n++;
         };
         const uint32_t dp = a.dprime[r];
-        if (nc >= (uint32_t)R && nc > 0 && use_pos(nc, dp, R, a.l, a.method)) {
+        if (nc >= (uint32_t)R && nc > 0 && use_pos(nc, dp, R, a.l, a.method, a.pos_unit)) {
             const uint32_t rows = dp - a.l + 1;
             const unsigned long long cap = 4 * a.item_cost;
             uint32_t rb = 0;
             unsigned long long acc = 0;
             for (uint32_t q1 = 0; q1 < rows; q1++) {
-                unsigned long long c = pos_row_cost(nc, dp, q1, a.l);
+                unsigned long long c = pos_row_cost(nc, dp, q1, a.l, a.pos_unit);
                 if (q1 > rb && (acc + c > cap || q1 - rb >= (uint32_t)ROWS_MAX)) {
                     emit(rb, q1, 0, POS_ITEM, acc);
                     rb = q1;
@@ -935,7 +1099,7 @@ __global__ void k_items(ItemArgs a) {
 
 constexpr int PB_THREADS = 256;
 constexpr int PB_WARPS = PB_THREADS / 32;
-constexpr int PB_SMEM_WORDS = PB_SMEM_WORDS_PLAN;  // 96 KB of staged words
+constexpr int PB_SMEM_WORDS = PB_SMEM_WORDS_PLAN;  // 64 KB of staged words
 constexpr size_t PB_SMEM = PB_SMEM_WORDS * 4;
 constexpr int SCRATCH_SLOTS = 7;  // per-warp mask slots for wide anchors (>= max(R, 6))
 
@@ -947,6 +1111,9 @@ struct TupleArgs {
     const uint32_t *iorder;
     Counters *cnt;
     unsigned long long *per_anchor;  // u128 per anchor rank, or null
+    unsigned long long *per_graph;   // u128 per graph of a batch, or null
+    const int64_t *graph_x0;         // first anchor rank of each graph (n_graphs + 1)
+    int n_graphs;
     uint32_t *wide_scratch;          // per warp: R * wmax words
     uint32_t wmax;
     int l;
@@ -1621,6 +1788,110 @@ __device__ void pos_expand(const uint32_t *cm, uint32_t dp, uint32_t wc, const u
     }
 }
 
+// Lane groups for narrow position-side masks (wc <= G <= 32 candidate
+// words): each group of G lanes holds one copy of the prefix (word lane % G)
+// and the 32/G groups of the warp test 32/G extensions q at once.
+template <int R, int G, int LEV>
+__device__ void pos_expand_g(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t m0, uint32_t m1,
+                             uint32_t start, int l, Acc &acc, unsigned *err) {
+    constexpr int NG = 32 / G;
+    const int lane = threadIdx.x & 31, grp = lane / G, wl = lane % G;
+    const int last = (int)dp - 1 - (l - LEV);
+    for (int qb = (int)start; qb <= last; qb += NG) {
+        const int q = qb + grp;
+        const bool valid = q <= last;
+        uint32_t x0 = 0, x1 = 0;
+        if (valid && (uint32_t)wl < wc) {
+            x0 = m0 & cm[(size_t)q * wc + wl];
+            x1 = m1 & cm[(size_t)(dp + q) * wc + wl];
+        }
+        uint32_t n = __popc(x0) + __popc(x1);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) n += __shfl_xor_sync(FULL, n, o);
+        const bool lead = valid && wl == 0;
+        if (lead) {
+            acc.tested++;
+            acc.words += 2ull * wc;
+        }
+        if (LEV == l) {
+            if (lead && n >= (uint32_t)R) {
+                acc.leaves++;
+                binom_add_r<R>(acc.sum, n, err);
+            }
+        } else if constexpr (LEV < 8) {
+            uint32_t bal = __ballot_sync(FULL, lead && n >= (uint32_t)R);
+            while (bal) {
+                const int sl = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const int gs = sl / G;
+                const uint32_t y0 = __shfl_sync(FULL, x0, gs * G + wl);
+                const uint32_t y1 = __shfl_sync(FULL, x1, gs * G + wl);
+                pos_expand_g<R, G, LEV + 1>(cm, dp, wc, y0, y1, (uint32_t)(qb + gs) + 1, l, acc, err);
+            }
+        }
+    }
+}
+
+// A position-side unit: first position q1 and, when l >= 3, second position
+// q2 (q2 == 0 means the unit is the whole row q1, used when l == 2).
+template <int R, int G>
+__device__ void pos_unit_g(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
+                           int l, Acc &acc, unsigned *err) {
+    const int wl = (threadIdx.x & 31) % G;
+    uint32_t m0 = 0, m1 = 0;
+    if ((uint32_t)wl < wc) {
+        m0 = cm[(size_t)q1 * wc + wl];
+        m1 = cm[(size_t)(dp + q1) * wc + wl];
+        if (q2) {
+            m0 &= cm[(size_t)q2 * wc + wl];
+            m1 &= cm[(size_t)(dp + q2) * wc + wl];
+        }
+    }
+    uint32_t n = __popc(m0) + __popc(m1);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) n += __shfl_xor_sync(FULL, n, o);
+    if (n < (uint32_t)R) return;
+    if (q2) pos_expand_g<R, G, 3>(cm, dp, wc, m0, m1, q2 + 1, l, acc, err);
+    else pos_expand_g<R, G, 2>(cm, dp, wc, m0, m1, q1 + 1, l, acc, err);
+}
+
+// Wide position-side masks (wc > 32): WPL words per lane, whole warp per node.
+template <int R, int WPL>
+__device__ void pos_unit_w(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
+                           int l, Acc &acc, unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    uint32_t M0[WPL], M1[WPL];
+    uint32_t n = 0;
+#pragma unroll
+    for (int k = 0; k < WPL; k++) {
+        const uint32_t w = lane + 32 * k;
+        M0[k] = w < wc ? cm[(size_t)q1 * wc + w] : 0u;
+        M1[k] = w < wc ? cm[(size_t)(dp + q1) * wc + w] : 0u;
+        if (q2 && w < wc) {
+            M0[k] &= cm[(size_t)q2 * wc + w];
+            M1[k] &= cm[(size_t)(dp + q2) * wc + w];
+        }
+        n += __popc(M0[k]) + __popc(M1[k]);
+    }
+    n = __reduce_add_sync(FULL, n);
+    if (n < (uint32_t)R) return;
+    if (q2) pos_expand<R, WPL, 3>(cm, dp, wc, M0, M1, q2 + 1, l, acc, err);
+    else pos_expand<R, WPL, 2>(cm, dp, wc, M0, M1, q1 + 1, l, acc, err);
+}
+
+template <int R>
+__device__ void pos_unit(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
+                         int l, Acc &acc, unsigned *err) {
+    if (wc <= 1) pos_unit_g<R, 1>(cm, dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 2) pos_unit_g<R, 2>(cm, dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 4) pos_unit_g<R, 4>(cm, dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 8) pos_unit_g<R, 8>(cm, dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 16) pos_unit_g<R, 16>(cm, dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 32) pos_unit_g<R, 32>(cm, dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 64) pos_unit_w<R, 2>(cm, dp, wc, q1, q2, l, acc, err);
+    else pos_unit_w<R, 4>(cm, dp, wc, q1, q2, l, acc, err);
+}
+
 // First position q1 of a position-side item.
 template <int R, int WPL>
 __device__ void pos_row(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q1, int l, Acc &acc,
@@ -1641,7 +1912,7 @@ __device__ void pos_row(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q
 }
 
 template <int R>
-__global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
+__global__ void __launch_bounds__(PB_THREADS, 3) k_tuples(TupleArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ int s_item;
     __shared__ uint32_t s_unit, s_total;
@@ -1678,7 +1949,6 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
             const uint32_t dp = a.dprime[r];
             const uint32_t wc = (nc + 31) / 32;
             for (uint32_t t = tid; t < 2 * dp * wc; t += PB_THREADS) sm[t] = 0;
-            if (tid == 0) s_unit = it.i0;
             __syncthreads();
             for (uint32_t c = tid; c < nc; c += PB_THREADS) {
                 const uint32_t cb = 1u << (c & 31), cw = c >> 5;
@@ -1694,15 +1964,32 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
                     }
                 }
             }
+            // units: rows q1 (l == 2) or pairs (q1, q2) with q2 <= dp - l + 1
+            if (tid == 0) {
+                uint32_t acc_u = 0;
+                for (uint32_t q = it.i0; q < it.i1; q++) {
+                    s_rowpre[q - it.i0] = acc_u;
+                    acc_u += a.l == 2 ? 1u : (dp - a.l + 1 - q);
+                }
+                s_rowpre[it.i1 - it.i0] = acc_u;
+                s_total = acc_u;
+                s_unit = 0;
+            }
             __syncthreads();
+            const uint32_t total = s_total;
             for (;;) {
-                uint32_t q1 = 0;
-                if (lane == 0) q1 = atomicAdd(&s_unit, 1u);
-                q1 = __shfl_sync(FULL, q1, 0);
-                if (q1 >= it.i1) break;
-                if (wc <= 32) pos_row<R, 1>(sm, dp, wc, q1, a.l, acc, err);
-                else if (wc <= 64) pos_row<R, 2>(sm, dp, wc, q1, a.l, acc, err);
-                else pos_row<R, 4>(sm, dp, wc, q1, a.l, acc, err);
+                uint32_t u = 0;
+                if (lane == 0) u = atomicAdd(&s_unit, 1u);
+                u = __shfl_sync(FULL, u, 0);
+                if (u >= total) break;
+                uint32_t lo = 0, hi = it.i1 - it.i0;
+                while (hi - lo > 1) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if (s_rowpre[mid] <= u) lo = mid; else hi = mid;
+                }
+                const uint32_t q1 = it.i0 + lo;
+                const uint32_t q2 = a.l == 2 ? 0u : q1 + 1 + (u - s_rowpre[lo]);
+                pos_unit<R>(sm, dp, wc, q1, q2, a.l, acc, err);
             }
         } else {
         Masks m;
@@ -1787,6 +2074,14 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
         if (lane == 0 && (ws.lo | ws.hi)) {
             atomic_add_u128(a.cnt->total, ws.lo, ws.hi);
             if (a.per_anchor) atomic_add_u128(a.per_anchor + 2 * (size_t)r, ws.lo, ws.hi);
+            if (a.per_graph) {
+                int lo = 0, hi = a.n_graphs;  // largest g with graph_x0[g] <= r
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (a.graph_x0[mid] <= (int64_t)r) lo = mid; else hi = mid;
+                }
+                atomic_add_u128(a.per_graph + 2 * (size_t)lo, ws.lo, ws.hi);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -1808,6 +2103,10 @@ __global__ void __launch_bounds__(PB_THREADS) k_tuples(TupleArgs a) {
 // ------------------------------------------------------------------ host side
 
 namespace {
+
+// Relative cost of one position-side prefix node (per candidate word per
+// lane) against one candidate-side tuple word; measured on GB300.
+constexpr unsigned long long kPosNodeCost = 6;
 
 // Largest x with binom(x, l) computable in 64 bits by the multiplicative
 // formula: every partial product binom(x-l+i, i) * i must stay below 2^64.
@@ -1867,6 +2166,9 @@ int blocks_per_sm(const void *fn, int threads, size_t smem) {
     return n < 1 ? 1 : n;
 }
 
+
+}  // namespace
+
 struct EventTimer {
     cudaEvent_t e[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool on;
@@ -1888,7 +2190,326 @@ struct EventTimer {
     }
 };
 
-}  // namespace
+struct CountRun {
+    const Orient *o = nullptr;
+    int64_t nnz = 0, nX = 0;
+    CountSpec spec;
+    int R = 0;
+    cudaStream_t s = nullptr;
+    DevBuf<Counters> cnt;
+    DevBuf<uint32_t> A_bit, dprime, rsv_c, skey, sval, tk, tv, ncand, npaper, pool, ikey, ival, t1,
+        t2, scratch;
+    DevBuf<unsigned long long> e_use, e_all, bucket, per;
+    DevBuf<int64_t> pool_off, dtot, item_off;
+    DevBuf<Item> items;
+    TwohopArgs ta;
+    TupleArgs tu;
+    int ga = 0, gs = 0, gt = 0;
+    int64_t n_items = 0;
+    Counters hc;
+    CountResult res;
+
+    // Launches that execute a planned count (no host synchronisation, no
+    // allocation): usable under stream capture.
+    void launch_count(bool timed, EventTimer *tm) {
+        SBC_CUDA(cudaMemsetAsync(&cnt.ptr->run_begin, 0,
+                                 sizeof(Counters) - offsetof(Counters, run_begin), s));
+        if (per.ptr) SBC_CUDA(cudaMemsetAsync(per.ptr, 0, per.bytes(), s));
+        if (spec.per_graph) SBC_CUDA(cudaMemsetAsync(spec.per_graph, 0, 16 * (size_t)spec.n_graphs, s));
+        if (timed) tm->mark(1, s);
+        if (ga > 0) {
+            if (spec.paper) k_twohop_large<true><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
+            else k_twohop_large<false><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
+            SBC_LAUNCHED();
+            g_launches++;
+        }
+        if (gs > 0) {
+            if (spec.paper) k_twohop_small<true><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
+            else k_twohop_small<false><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
+            SBC_LAUNCHED();
+            g_launches++;
+        }
+        if (timed) tm->mark(2, s);
+        if (timed) tm->mark(3, s);
+        if (gt > 0) {
+            switch (R) {
+                case 1: launch_tuples<1>(gt, s, tu); break;
+                case 2: launch_tuples<2>(gt, s, tu); break;
+                case 3: launch_tuples<3>(gt, s, tu); break;
+                case 4: launch_tuples<4>(gt, s, tu); break;
+                case 5: launch_tuples<5>(gt, s, tu); break;
+                case 6: launch_tuples<6>(gt, s, tu); break;
+                default: launch_tuples<7>(gt, s, tu); break;
+            }
+            g_launches++;
+        }
+        if (timed) tm->mark(4, s);
+    }
+
+    // Plan (with host reads of sizes) and execute once.
+    void plan_and_run(EventTimer *tm) {
+        const int B = 256;
+        const int l = spec.l;
+        R = spec.k - 1;
+        unsigned long long lim[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 2; i <= 8; i++) lim[i] = binom64_limit(i);
+        SBC_CUDA(cudaMemcpyToSymbolAsync(c_binom64_max, lim, sizeof(lim), 0, cudaMemcpyHostToDevice, s));
+        cnt.alloc(1, s);
+        SBC_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(Counters), s));
+        A_bit.alloc(nnz, s);
+        dprime.alloc(nX, s);
+        rsv_c.alloc(nX, s);
+        skey.alloc(nX, s);
+        sval.alloc(nX, s);
+        tk.alloc(nX, s);
+        tv.alloc(nX, s);
+        ncand.alloc(nX, s);
+        npaper.alloc(spec.paper ? nX : 0, s);
+        e_use.alloc(nX, s);
+        e_all.alloc(nX, s);
+        pool_off.alloc(nX + 1, s);
+        dtot.alloc(1, s);
+        k_plan<<<grid_for(nX * 32, B), B, 0, s>>>(o->A_off.ptr, o->A_ent.ptr, o->A_pos.ptr,
+                                                  o->B_off.ptr, nX, R, l, spec.shard, spec.nshard,
+                                                  spec.paper ? 1 : 0, A_bit.ptr, dprime.ptr,
+                                                  e_use.ptr, e_all.ptr, rsv_c.ptr, pool_off.ptr,
+                                                  skey.ptr, sval.ptr, cnt.ptr, SMALL_E);
+        SBC_LAUNCHED();
+        g_launches++;
+        scan_exclusive_i64(pool_off.ptr, pool_off.ptr, nX + 1, dtot.ptr, s);
+        radix_sort_pairs(skey.ptr, sval.ptr, tk.ptr, tv.ptr, nX, 32, s);
+        SBC_CUDA(cudaMemsetAsync(ncand.ptr, 0, (size_t)nX * 4, s));
+        if (spec.paper) SBC_CUDA(cudaMemsetAsync(npaper.ptr, 0, (size_t)nX * 4, s));
+        int64_t pool_words = 0;
+        SBC_CUDA(cudaMemcpyAsync(&pool_words, dtot.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        SBC_CUDA(cudaStreamSynchronize(s));
+        pool.alloc((size_t)(pool_words > 0 ? pool_words : 1), s);
+        const int sms = sm_count();
+
+        ta.A_off = o->A_off.ptr;
+        ta.A_ent = o->A_ent.ptr;
+        ta.A_pos = o->A_pos.ptr;
+        ta.A_bit = A_bit.ptr;
+        ta.B_off = o->B_off.ptr;
+        ta.B_ent = o->B_ent.ptr;
+        ta.dprime = dprime.ptr;
+        ta.e_use = e_use.ptr;
+        ta.e_all = e_all.ptr;
+        ta.rsv_c = rsv_c.ptr;
+        ta.pool_off = pool_off.ptr;
+        ta.order = sval.ptr;
+        ta.pool = pool.ptr;
+        ta.ncand = ncand.ptr;
+        ta.npaper = spec.paper ? npaper.ptr : nullptr;
+        ta.cnt = cnt.ptr;
+        ta.l = l;
+        ta.bucket = nullptr;
+        ta.bucket_slot = 0;
+        if (hc.n_big > 0) {
+            const void *fn = spec.paper ? (const void *)k_twohop_large<true> : (const void *)k_twohop_large<false>;
+            ga = sms * blocks_per_sm(fn, PL_THREADS, PL_SMEM);
+            if ((int64_t)ga > (int64_t)hc.n_big) ga = (int)hc.n_big;
+            if (hc.e_max > (unsigned long long)PL_WCAP) {
+                const int lgb = bucket_lg(hc.e_max);
+                ta.bucket_slot = bucket_cap(hc.e_max, lgb) << lgb;
+                bucket.alloc((size_t)ga * ta.bucket_slot, s);
+                ta.bucket = bucket.ptr;
+            }
+        }
+        if (hc.n_active > hc.n_big) {
+            const void *fn = spec.paper ? (const void *)k_twohop_small<true> : (const void *)k_twohop_small<false>;
+            gs = sms * blocks_per_sm(fn, PS_THREADS, PS_SMEM);
+            int64_t need = ((int64_t)hc.n_active - hc.n_big + PS_WARPS - 1) / PS_WARPS;
+            if ((int64_t)gs > need) gs = (int)need;
+        }
+        // the 2-hop kernels of the first execution
+        if (tm) tm->mark(1, s);
+        if (ga > 0) {
+            if (spec.paper) k_twohop_large<true><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
+            else k_twohop_large<false><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
+            SBC_LAUNCHED();
+            g_launches++;
+        }
+        if (gs > 0) {
+            if (spec.paper) k_twohop_small<true><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
+            else k_twohop_small<false><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
+            SBC_LAUNCHED();
+            g_launches++;
+        }
+        if (tm) tm->mark(2, s);
+
+        // tuple phase planning (needs the candidate counts)
+        ItemArgs ia;
+        ia.ncand = ncand.ptr;
+        ia.npaper = spec.paper ? npaper.ptr : nullptr;
+        ia.dprime = dprime.ptr;
+        ia.nX = nX;
+        ia.R = R;
+        ia.l = l;
+        ia.method = spec.method;
+        ia.pos_unit = spec.pos_unit;
+        ia.cnt = cnt.ptr;
+        ia.item_cost = 0;
+        ia.item_off = nullptr;
+        ia.item_cnt = nullptr;
+        ia.items = nullptr;
+        ia.ikey = ia.ival = nullptr;
+        k_anchor_cost<<<grid_for(nX, B), B, 0, s>>>(ia);
+        SBC_LAUNCHED();
+        g_launches++;
+        SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        SBC_CUDA(cudaStreamSynchronize(s));
+        const int gb = sms * blocks_per_sm((const void *)k_tuples<1>, PB_THREADS, PB_SMEM);
+        unsigned long long ic = hc.cost_total / ((unsigned long long)gb * PB_WARPS * 4ull);
+        if (ic < (1ull << 12)) ic = 1ull << 12;
+        if (ic > (1ull << 30)) ic = 1ull << 30;
+        ia.item_cost = ic;
+        item_off.alloc(nX + 1, s);
+        ia.item_cnt = item_off.ptr;
+        n_items = 0;
+        if (hc.cost_total > 0 || R == 1) {
+            k_items<false><<<grid_for(nX, B), B, 0, s>>>(ia);
+            SBC_LAUNCHED();
+            scan_exclusive_i64(item_off.ptr, item_off.ptr, nX + 1, dtot.ptr, s);
+            g_launches++;
+            SBC_CUDA(cudaMemcpyAsync(&n_items, dtot.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            SBC_CUDA(cudaStreamSynchronize(s));
+        }
+        if (n_items > 0xFFFFFFF0ll) fail(SBC_E_UNSUPPORTED, "too many work items");
+        if (tm) tm->mark(3, s);
+        if (n_items > 0) {
+            items.alloc(n_items, s);
+            ikey.alloc(n_items, s);
+            ival.alloc(n_items, s);
+            t1.alloc(n_items, s);
+            t2.alloc(n_items, s);
+            ia.item_off = item_off.ptr;
+            ia.items = items.ptr;
+            ia.ikey = ikey.ptr;
+            ia.ival = ival.ptr;
+            k_items<true><<<grid_for(nX, B), B, 0, s>>>(ia);
+            SBC_LAUNCHED();
+            g_launches++;
+            radix_sort_pairs(ikey.ptr, ival.ptr, t1.ptr, t2.ptr, n_items, 32, s);
+            unsigned ni = (unsigned)n_items;
+            SBC_CUDA(cudaMemcpyAsync(&cnt.ptr->n_items, &ni, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+            per.alloc(spec.per_anchor ? 2 * nX : 0, s);
+            if (per.ptr) SBC_CUDA(cudaMemsetAsync(per.ptr, 0, per.bytes(), s));
+            if (spec.per_graph) SBC_CUDA(cudaMemsetAsync(spec.per_graph, 0, 16 * (size_t)spec.n_graphs, s));
+            const uint32_t wmax = (uint32_t)((o->max_deg_x + 31) / 32);
+            gt = gb;
+            if ((int64_t)gt > n_items) gt = (int)n_items;
+            scratch.alloc(wmax > 8 ? (size_t)gt * PB_WARPS * SCRATCH_SLOTS * wmax : 0, s);
+            tu.ncand = ncand.ptr;
+            tu.dprime = dprime.ptr;
+            tu.rsv_c = rsv_c.ptr;
+            tu.pool_off = pool_off.ptr;
+            tu.pool = pool.ptr;
+            tu.items = items.ptr;
+            tu.iorder = ival.ptr;
+            tu.cnt = cnt.ptr;
+            tu.per_anchor = per.ptr;
+            tu.per_graph = spec.per_graph;
+            tu.graph_x0 = spec.graph_x0;
+            tu.n_graphs = spec.n_graphs;
+            tu.wide_scratch = scratch.ptr;
+            tu.wmax = wmax;
+            tu.l = l;
+            switch (R) {
+                case 1: launch_tuples<1>(gt, s, tu); break;
+                case 2: launch_tuples<2>(gt, s, tu); break;
+                case 3: launch_tuples<3>(gt, s, tu); break;
+                case 4: launch_tuples<4>(gt, s, tu); break;
+                case 5: launch_tuples<5>(gt, s, tu); break;
+                case 6: launch_tuples<6>(gt, s, tu); break;
+                default: launch_tuples<7>(gt, s, tu); break;
+            }
+            g_launches++;
+        } else if (spec.per_graph) {
+            SBC_CUDA(cudaMemsetAsync(spec.per_graph, 0, 16 * (size_t)spec.n_graphs, s));
+        }
+        if (tm) tm->mark(4, s);
+        collect();
+        // planning scratch that a replay does not need
+        skey.release();
+        tk.release();
+        tv.release();
+        item_off.release();
+        ikey.release();
+        t1.release();
+        t2.release();
+    }
+
+    // Read the counters after an execution (synchronises the stream).
+    void collect() {
+        SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        SBC_CUDA(cudaStreamSynchronize(s));
+        if (hc.err & CERR_OVERFLOW) fail(SBC_E_OVERFLOW, "balanced biclique count exceeds 128 bits");
+        if (hc.err & (CERR_RESERVE | CERR_HASH))
+            fail(SBC_E_CUDA, "internal error in the 2-hop kernel (flags 0x%x)", hc.err);
+        res.count.lo = hc.total[0];
+        res.count.hi = hc.total[1];
+        const unsigned long long *tt = spec.paper ? hc.tuples_paper : hc.tuples_ours;
+        res.anchor_tuples.lo = tt[0];
+        res.anchor_tuples.hi = tt[1];
+        res.candidates = hc.candidates;
+        res.wedges = hc.wedges;
+        res.work_items = (uint64_t)n_items;
+        res.tested = hc.tested;
+        res.typed = hc.leaves;
+        res.popc_words = hc.popc_words;
+    }
+};
+
+CountRun *countrun_create(const Orient &o, int64_t nnz, const CountSpec &spec, cudaStream_t s,
+                          EventTimer *tm) {
+    if (o.max_deg_x >= (1ll << 21))
+        fail(SBC_E_UNSUPPORTED, "anchor-side degree %lld exceeds the 2^21 - 1 limit of the 2-hop counters",
+             (long long)o.max_deg_x);
+    ensure_kernel_attrs();
+    std::unique_ptr<CountRun> run(new CountRun());
+    run->o = &o;
+    run->nnz = nnz;
+    run->nX = o.nX;
+    run->spec = spec;
+    run->s = s;
+    if (nnz > 0 && o.nX > 0) run->plan_and_run(tm);
+    return run.release();
+}
+
+const CountResult &countrun_result(const CountRun *r) { return r->res; }
+
+void countrun_launch(CountRun *r, cudaStream_t s) {
+    if (r->nnz == 0 || r->nX == 0) {
+        if (r->spec.per_graph) SBC_CUDA(cudaMemsetAsync(r->spec.per_graph, 0, 16 * (size_t)r->spec.n_graphs, s));
+        return;
+    }
+    cudaStream_t keep = r->s;
+    r->s = s;
+    r->ta.cnt = r->cnt.ptr;
+    r->launch_count(false, nullptr);
+    r->s = keep;
+}
+
+void countrun_collect(CountRun *r, cudaStream_t s) {
+    if (r->nnz == 0 || r->nX == 0) return;
+    cudaStream_t keep = r->s;
+    r->s = s;
+    r->collect();
+    r->s = keep;
+}
+
+void countrun_destroy(CountRun *r) { delete r; }
+
+unsigned long long pos_node_cost_setting() {
+    unsigned long long u = kPosNodeCost;
+    if (const char *e = getenv("SBC_POS_NODE_COST")) {  // tuning override
+        long long v = atoll(e);
+        if (v > 0) u = (unsigned long long)v;
+    }
+    return u;
+}
 
 void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
                  sbc_count_stats *stats, cudaStream_t s) {
@@ -1900,12 +2521,18 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     int side = opts ? opts->anchor_side : SBC_SIDE_AUTO;
     if (side == SBC_SIDE_AUTO) side = g->wedges_u <= g->wedges_v ? 0 : 1;
     if (side != 0 && side != 1) fail(SBC_E_INVAL, "anchor_side must be -1, 0 or 1");
-    const int k = side == 0 ? p : q, l = side == 0 ? q : p, R = k - 1;
-    const bool paper = opts && (opts->flags & SBC_COUNT_PAPER_TUPLES);
-    const int shard = opts ? opts->shard : 0;
-    const int nshard = opts ? opts->shard_count : 0;
-    if (nshard < 0 || (nshard > 0 && (shard < 0 || shard >= nshard)))
-        fail(SBC_E_INVAL, "bad shard %d of %d", shard, nshard);
+    CountSpec spec;
+    spec.k = side == 0 ? p : q;
+    spec.l = side == 0 ? q : p;
+    spec.paper = opts && (opts->flags & SBC_COUNT_PAPER_TUPLES);
+    spec.shard = opts ? opts->shard : 0;
+    spec.nshard = opts ? opts->shard_count : 0;
+    spec.method = (opts && (opts->flags & SBC_COUNT_CANDIDATE_SIDE)) ? 1
+                : (opts && (opts->flags & SBC_COUNT_POSITION_SIDE)) ? 2 : 0;
+    spec.pos_unit = pos_node_cost_setting();
+    spec.per_anchor = opts && opts->per_anchor;
+    if (spec.nshard < 0 || (spec.nshard > 0 && (spec.shard < 0 || spec.shard >= spec.nshard)))
+        fail(SBC_E_INVAL, "bad shard %d of %d", spec.shard, spec.nshard);
     const int64_t kernels0 = g_launches.load();
     if (stats) {
         memset(stats, 0, sizeof(*stats));
@@ -1914,7 +2541,6 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     const int64_t nX = side == 0 ? g->n_u : g->n_v;
     if (opts && opts->per_anchor && nX > 0) memset(opts->per_anchor, 0, sizeof(sbc_u128) * (size_t)nX);
     if (g->nnz == 0 || nX == 0) return;
-    ensure_kernel_attrs();
     EventTimer tm(stats != nullptr && !thread_arena_active());
     tm.mark(0, s);
     {
@@ -1922,206 +2548,35 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
         build_orientation(g, side, s);
     }
     const Orient &o = g->side[side];
-    const int64_t nnz = g->nnz;
-    const int B = 256;
-    if (o.max_deg_x >= (1ll << 21))
-        fail(SBC_E_UNSUPPORTED, "anchor-side degree %lld exceeds the 2^21 - 1 limit of the 2-hop counters",
-             (long long)o.max_deg_x);
-
-    unsigned long long lim[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = 2; i <= 8; i++) lim[i] = binom64_limit(i);
-    SBC_CUDA(cudaMemcpyToSymbolAsync(c_binom64_max, lim, sizeof(lim), 0, cudaMemcpyHostToDevice, s));
-
-    DevBuf<Counters> cnt(1, s);
-    SBC_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(Counters), s));
-    DevBuf<uint32_t> A_bit(nnz, s), dprime(nX, s), rsv_c(nX, s), skey(nX, s), sval(nX, s),
-        tk(nX, s), tv(nX, s), ncand(nX, s), npaper(paper ? nX : 0, s);
-    DevBuf<unsigned long long> e_use(nX, s), e_all(nX, s);
-    DevBuf<int64_t> pool_off(nX + 1, s), dtot(1, s);
-
-    k_plan<<<grid_for(nX * 32, B), B, 0, s>>>(o.A_off.ptr, o.A_ent.ptr, o.A_pos.ptr, o.B_off.ptr, nX,
-                                              R, l, shard, nshard, paper ? 1 : 0, A_bit.ptr,
-                                              dprime.ptr, e_use.ptr, e_all.ptr, rsv_c.ptr,
-                                              pool_off.ptr, skey.ptr, sval.ptr, cnt.ptr, SMALL_E);
-    SBC_LAUNCHED();
-    g_launches++;
-    scan_exclusive_i64(pool_off.ptr, pool_off.ptr, nX + 1, dtot.ptr, s);
-    radix_sort_pairs(skey.ptr, sval.ptr, tk.ptr, tv.ptr, nX, 32, s);
-    SBC_CUDA(cudaMemsetAsync(ncand.ptr, 0, (size_t)nX * 4, s));
-    if (paper) SBC_CUDA(cudaMemsetAsync(npaper.ptr, 0, (size_t)nX * 4, s));
-    int64_t pool_words = 0;
-    Counters hc;
-    SBC_CUDA(cudaMemcpyAsync(&pool_words, dtot.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-    SBC_CUDA(cudaStreamSynchronize(s));
-    DevBuf<uint32_t> pool((size_t)(pool_words > 0 ? pool_words : 1), s);
-    tm.mark(1, s);
-
-    const int sms = sm_count();
-    if (hc.n_active > 0) {
-        TwohopArgs ta;
-        ta.A_off = o.A_off.ptr;
-        ta.A_ent = o.A_ent.ptr;
-        ta.A_pos = o.A_pos.ptr;
-        ta.A_bit = A_bit.ptr;
-        ta.B_off = o.B_off.ptr;
-        ta.B_ent = o.B_ent.ptr;
-        ta.dprime = dprime.ptr;
-        ta.e_use = e_use.ptr;
-        ta.e_all = e_all.ptr;
-        ta.rsv_c = rsv_c.ptr;
-        ta.pool_off = pool_off.ptr;
-        ta.order = sval.ptr;
-        ta.pool = pool.ptr;
-        ta.ncand = ncand.ptr;
-        ta.npaper = paper ? npaper.ptr : nullptr;
-        ta.cnt = cnt.ptr;
-        ta.l = l;
-        if (hc.n_big > 0) {
-            const void *fn = paper ? (const void *)k_twohop_large<true> : (const void *)k_twohop_large<false>;
-            int ga = sms * blocks_per_sm(fn, PL_THREADS, PL_SMEM);
-            if ((int64_t)ga > (int64_t)hc.n_big) ga = (int)hc.n_big;
-            if (paper) k_twohop_large<true><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
-            else k_twohop_large<false><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
-            SBC_LAUNCHED();
-            g_launches++;
-        }
-        if (hc.n_active > hc.n_big) {
-            const void *fn = paper ? (const void *)k_twohop_small<true> : (const void *)k_twohop_small<false>;
-            int gs = sms * blocks_per_sm(fn, PS_THREADS, PS_SMEM);
-            int64_t need = ((int64_t)hc.n_active - hc.n_big + PS_WARPS - 1) / PS_WARPS;
-            if ((int64_t)gs > need) gs = (int)need;
-            if (paper) k_twohop_small<true><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
-            else k_twohop_small<false><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
-            SBC_LAUNCHED();
-            g_launches++;
-        }
-    }
-    tm.mark(2, s);
-
-    // tuple phase planning
-    ItemArgs ia;
-    ia.ncand = ncand.ptr;
-    ia.npaper = paper ? npaper.ptr : nullptr;
-    ia.dprime = dprime.ptr;
-    ia.nX = nX;
-    ia.R = R;
-    ia.l = l;
-    ia.method = (opts && (opts->flags & SBC_COUNT_CANDIDATE_SIDE)) ? 1
-              : (opts && (opts->flags & SBC_COUNT_POSITION_SIDE)) ? 2 : 0;
-    ia.cnt = cnt.ptr;
-    ia.item_cost = 0;
-    ia.item_off = nullptr;
-    ia.item_cnt = nullptr;
-    ia.items = nullptr;
-    ia.ikey = ia.ival = nullptr;
-    k_anchor_cost<<<grid_for(nX, B), B, 0, s>>>(ia);
-    SBC_LAUNCHED();
-    g_launches++;
-    SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-    SBC_CUDA(cudaStreamSynchronize(s));
-    const int gb = sms * blocks_per_sm((const void *)k_tuples<1>, PB_THREADS, PB_SMEM);
-    unsigned long long ic = hc.cost_total / ((unsigned long long)gb * PB_WARPS * 4ull);
-    if (ic < (1ull << 12)) ic = 1ull << 12;
-    if (ic > (1ull << 30)) ic = 1ull << 30;
-    ia.item_cost = ic;
-    DevBuf<int64_t> item_off(nX + 1, s);
-    ia.item_cnt = item_off.ptr;
-    int64_t n_items = 0;
-    if (hc.cost_total > 0 || R == 1) {
-        k_items<false><<<grid_for(nX, B), B, 0, s>>>(ia);
-        SBC_LAUNCHED();
-        scan_exclusive_i64(item_off.ptr, item_off.ptr, nX + 1, dtot.ptr, s);
-        g_launches++;
-        SBC_CUDA(cudaMemcpyAsync(&n_items, dtot.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    std::unique_ptr<CountRun> run(countrun_create(o, g->nnz, spec, s, tm.on ? &tm : nullptr));
+    const CountResult &res = run->res;
+    if (spec.per_anchor && run->per.ptr) {
+        std::vector<unsigned long long> hp((size_t)2 * nX);
+        std::vector<int32_t> vo((size_t)nX);
+        SBC_CUDA(cudaMemcpyAsync(hp.data(), run->per.ptr, run->per.bytes(), cudaMemcpyDeviceToHost, s));
+        SBC_CUDA(cudaMemcpyAsync(vo.data(), o.vert_of.ptr, (size_t)nX * 4, cudaMemcpyDeviceToHost, s));
         SBC_CUDA(cudaStreamSynchronize(s));
-    }
-    if (n_items > 0xFFFFFFF0ll) fail(SBC_E_UNSUPPORTED, "too many work items");
-    if (n_items > 0) {
-        DevBuf<Item> items(n_items, s);
-        DevBuf<uint32_t> ikey(n_items, s), ival(n_items, s), t1(n_items, s), t2(n_items, s);
-        ia.item_off = item_off.ptr;
-        ia.items = items.ptr;
-        ia.ikey = ikey.ptr;
-        ia.ival = ival.ptr;
-        k_items<true><<<grid_for(nX, B), B, 0, s>>>(ia);
-        SBC_LAUNCHED();
-        g_launches++;
-        radix_sort_pairs(ikey.ptr, ival.ptr, t1.ptr, t2.ptr, n_items, 32, s);
-        unsigned ni = (unsigned)n_items;
-        SBC_CUDA(cudaMemcpyAsync(&cnt.ptr->n_items, &ni, sizeof(unsigned), cudaMemcpyHostToDevice, s));
-        DevBuf<unsigned long long> per(opts && opts->per_anchor ? 2 * nX : 0, s);
-        if (per.ptr) SBC_CUDA(cudaMemsetAsync(per.ptr, 0, per.bytes(), s));
-        uint32_t wmax = (uint32_t)((o.max_deg_x + 31) / 32);
-        int grid = gb;
-        if ((int64_t)grid > n_items) grid = (int)n_items;
-        DevBuf<uint32_t> scratch(wmax > 8 ? (size_t)grid * PB_WARPS * SCRATCH_SLOTS * wmax : 0, s);
-        TupleArgs tu;
-        tu.ncand = ncand.ptr;
-        tu.dprime = dprime.ptr;
-        tu.rsv_c = rsv_c.ptr;
-        tu.pool_off = pool_off.ptr;
-        tu.pool = pool.ptr;
-        tu.items = items.ptr;
-        tu.iorder = ival.ptr;
-        tu.cnt = cnt.ptr;
-        tu.per_anchor = per.ptr;
-        tu.wide_scratch = scratch.ptr;
-        tu.wmax = wmax;
-        tu.l = l;
-        tm.mark(3, s);
-        switch (R) {
-            case 1: launch_tuples<1>(grid, s, tu); break;
-            case 2: launch_tuples<2>(grid, s, tu); break;
-            case 3: launch_tuples<3>(grid, s, tu); break;
-            case 4: launch_tuples<4>(grid, s, tu); break;
-            case 5: launch_tuples<5>(grid, s, tu); break;
-            case 6: launch_tuples<6>(grid, s, tu); break;
-            default: launch_tuples<7>(grid, s, tu); break;
+        for (int64_t r = 0; r < nX; r++) {
+            opts->per_anchor[vo[r]].lo = hp[2 * r];
+            opts->per_anchor[vo[r]].hi = hp[2 * r + 1];
         }
-        g_launches++;
-        tm.mark(4, s);
-        if (per.ptr) {
-            std::vector<unsigned long long> hp((size_t)2 * nX);
-            std::vector<int32_t> vo((size_t)nX);
-            SBC_CUDA(cudaMemcpyAsync(hp.data(), per.ptr, per.bytes(), cudaMemcpyDeviceToHost, s));
-            SBC_CUDA(cudaMemcpyAsync(vo.data(), o.vert_of.ptr, (size_t)nX * 4, cudaMemcpyDeviceToHost, s));
-            SBC_CUDA(cudaStreamSynchronize(s));
-            for (int64_t r = 0; r < nX; r++) {
-                opts->per_anchor[vo[r]].lo = hp[2 * r];
-                opts->per_anchor[vo[r]].hi = hp[2 * r + 1];
-            }
-        }
-    } else {
-        tm.mark(3, s);
-        tm.mark(4, s);
     }
-    SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-    SBC_CUDA(cudaStreamSynchronize(s));
-    if (hc.err & CERR_OVERFLOW) fail(SBC_E_OVERFLOW, "balanced biclique count exceeds 128 bits");
-    if (hc.err & (CERR_RESERVE | CERR_HASH))
-        fail(SBC_E_CUDA, "internal error in the 2-hop kernel (flags 0x%x)", hc.err);
     if (stats) {
-        stats->count.lo = hc.total[0];
-        stats->count.hi = hc.total[1];
-        if (paper) {
-            stats->anchor_tuples.lo = hc.tuples_paper[0];
-            stats->anchor_tuples.hi = hc.tuples_paper[1];
-        } else {
-            stats->anchor_tuples.lo = hc.tuples_ours[0];
-            stats->anchor_tuples.hi = hc.tuples_ours[1];
-        }
-        stats->candidates = hc.candidates;
-        stats->wedges = hc.wedges;
-        stats->work_items = (uint64_t)n_items;
-        stats->tuples_tested = hc.tested;
-        stats->tuples_typed = hc.leaves;
-        stats->popc_words = hc.popc_words;
+        stats->count = res.count;
+        stats->anchor_tuples = res.anchor_tuples;
+        stats->candidates = res.candidates;
+        stats->wedges = res.wedges;
+        stats->work_items = res.work_items;
+        stats->tuples_tested = res.tested;
+        stats->tuples_typed = res.typed;
+        stats->popc_words = res.popc_words;
         stats->kernels = (int32_t)(g_launches.load() - kernels0);
-        stats->ms_prepare = tm.ms(0, 1) + tm.ms(2, 3);
-        stats->ms_twohop = tm.ms(1, 2);
-        stats->ms_tuples = tm.ms(3, 4);
-        stats->ms_total = tm.ms(0, 4);
+        if (tm.on) {
+            stats->ms_prepare = tm.ms(0, 1) + tm.ms(2, 3);
+            stats->ms_twohop = tm.ms(1, 2);
+            stats->ms_tuples = tm.ms(3, 4);
+            stats->ms_total = tm.ms(0, 4);
+        }
     }
 }
 

@@ -179,6 +179,37 @@ sbc_graph *create_graph(int64_t n_u, int64_t n_v, int64_t nnz, const void *row_o
 void count_graph(const sbc_graph *g, int p, int q, const sbc_count_opts *opts,
                  sbc_count_stats *stats, cudaStream_t s);
 
+// One count over an orientation (count.cu): k = tuple size on the anchor
+// side, l = size on the other side.
+struct CountSpec {
+    int k = 0, l = 0;
+    bool paper = false;     // also count Algorithm 2's candidate sets
+    int method = 0;         // 0 cheaper side per anchor, 1 candidate side, 2 position side
+    unsigned long long pos_unit = 0;
+    int shard = 0, nshard = 0;
+    bool per_anchor = false;
+    unsigned long long *per_graph = nullptr;  // device, 2 words per graph (batches)
+    const int64_t *graph_x0 = nullptr;        // device, first anchor rank per graph
+    int n_graphs = 0;
+};
+struct CountResult {
+    sbc_u128 count{0, 0}, anchor_tuples{0, 0};
+    uint64_t candidates = 0, wedges = 0, work_items = 0, tested = 0, typed = 0, popc_words = 0;
+};
+struct CountRun;
+struct EventTimer;
+// Plans and executes the count once (synchronising for sizes).
+CountRun *countrun_create(const Orient &o, int64_t nnz, const CountSpec &spec, cudaStream_t s,
+                          EventTimer *tm);
+const CountResult &countrun_result(const CountRun *r);
+// Launches of one execution of a planned count: no allocation, no host
+// synchronisation, so they may be captured into a CUDA graph.
+void countrun_launch(CountRun *r, cudaStream_t s);
+// Reads the counters of the last execution (synchronises s).
+void countrun_collect(CountRun *r, cudaStream_t s);
+void countrun_destroy(CountRun *r);
+unsigned long long pos_node_cost_setting();
+
 }  // namespace sbc
 
 // ---------------------------------------------------------------- device helpers

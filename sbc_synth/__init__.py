@@ -8,10 +8,10 @@ Graph model (Section 5 of the paper evaluates on real signed bipartite graphs
 of power-law shape, Table 1; those datasets are not available, so seeded
 synthetic graphs of the same shape stand in for them):
 
-* Chung-Lu bipartite: side sizes n_u, n_v, m distinct edges. Expected weights
-  w_i proportional to (i+1)^(-1/(gamma-1)) on each side, scaled to sum m and
-  clipped at a cap (the excess is redistributed by rescaling the unclipped
-  weights until the sum is m again). Each edge draws its U end proportional to
+* Chung-Lu bipartite (sampled in C, synth.c): side sizes n_u, n_v, m distinct
+  edges. Expected weights w_i proportional to (i+1)^(-1/(gamma-1)) on each
+  side, scaled to sum m and clipped at a cap (the excess is redistributed by
+  rescaling the unclipped weights). Each edge draws its U end proportional to
   w_U and its V end proportional to w_V; duplicates are rejected (first draw
   wins) until exactly m distinct edges exist.
 * Vertex ids are then randomly permuted on both sides so that id order is not
@@ -25,10 +25,42 @@ depends only on the arguments, never on library versions.
 """
 from __future__ import annotations
 
+import concurrent.futures
+import ctypes
 import dataclasses
 import math
+import os
+import subprocess
 
 import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "synth.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libsbc_synth.so")
+_clib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C sampler (gcc -O2) into sbc_synth/_build/."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _c():
+    global _clib
+    if _clib is None:
+        lib = ctypes.CDLL(build())
+        vp, i64, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        lib.synth_chung_lu.restype = ctypes.c_int
+        lib.synth_chung_lu.argtypes = [ctypes.c_uint64, i64, i64, i64, f64, f64, f64, f64, vp, vp]
+        lib.synth_csr.restype = ctypes.c_int
+        lib.synth_csr.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp]
+        _clib = lib
+    return _clib
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -66,32 +98,6 @@ def uniform01(seed: int, stream: int, n: int, start: int = 0) -> np.ndarray:
     )
 
 
-def powerlaw_weights(n: int, gamma: float, total: float, cap: float) -> np.ndarray:
-    """Expected degrees (i+1)^(-1/(gamma-1)), sum `total`, each at most `cap`."""
-    if n == 0:
-        return np.zeros(0)
-    w = np.power(np.arange(1, n + 1, dtype=np.float64), -1.0 / (gamma - 1.0))
-    w *= total / w.sum()
-    cap = max(float(cap), total / n)
-    for _ in range(64):
-        over = w > cap
-        if not over.any():
-            break
-        w[over] = cap
-        free = ~over
-        rest = total - cap * over.sum()
-        s = w[free].sum()
-        if s <= 0 or rest <= 0:
-            break
-        w[free] *= rest / s
-    return w
-
-
-def _sample_index(cdf: np.ndarray, r: np.ndarray) -> np.ndarray:
-    idx = np.searchsorted(cdf, r * cdf[-1], side="right")
-    return np.minimum(idx, len(cdf) - 1).astype(np.int64)
-
-
 @dataclasses.dataclass
 class SignedBipartite:
     """Signed bipartite graph as CSR over U (rows) with V column ids.
@@ -122,46 +128,42 @@ class SignedBipartite:
 
 
 def from_edges(n_u: int, n_v: int, u, v, s, name: str = "") -> SignedBipartite:
-    """Build a CSR (rows sorted by v) from edge arrays; no duplicate check."""
-    u = np.asarray(u, dtype=np.int64)
-    v = np.asarray(v, dtype=np.int64)
-    s = np.asarray(s, dtype=np.int8)
-    order = np.lexsort((v, u))
-    u, v, s = u[order], v[order], s[order]
+    """Build a CSR (rows ascending in u, each row sorted by v) from edge
+    arrays; no duplicate check."""
+    u = np.ascontiguousarray(u, dtype=np.int64)
+    v = np.ascontiguousarray(v, dtype=np.int64)
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    m = u.shape[0]
     offsets = np.zeros(n_u + 1, dtype=np.int64)
-    np.cumsum(np.bincount(u, minlength=n_u), out=offsets[1:])
-    return SignedBipartite(n_u, n_v, offsets, v.astype(np.int32), s, name)
+    cols = np.zeros(m, dtype=np.int32)
+    sgn = np.zeros(m, dtype=np.int8)
+    if _c().synth_csr(n_u, m, u.ctypes.data, v.ctypes.data, s.ctypes.data, offsets.ctypes.data,
+                      cols.ctypes.data, sgn.ctypes.data):
+        raise MemoryError("CSR build failed")
+    return SignedBipartite(n_u, n_v, offsets, cols, sgn, name)
 
 
 def chung_lu_edges(seed, n_u, n_v, m, gamma_u, gamma_v, cap_u=None, cap_v=None):
-    """m distinct (u, v) pairs of a bipartite Chung-Lu graph, ids permuted."""
+    """m distinct (u, v) pairs of a bipartite Chung-Lu graph, ids permuted.
+
+    Expected degrees (i+1)^(-1/(gamma-1)) per side, scaled to m and capped
+    (default half the other side; excess spread by rescaling); endpoints drawn
+    proportionally (U from stream 1, V from stream 2); duplicates rejected,
+    first draw wins, until m distinct pairs; ids relabelled by random
+    permutations (streams 3 and 4). Runs in C (synth.c)."""
     if m > n_u * n_v:
         raise ValueError("more edges than vertex pairs")
     cap_u = 0.5 * n_v if cap_u is None else cap_u
     cap_v = 0.5 * n_u if cap_v is None else cap_v
-    cdf_u = np.cumsum(powerlaw_weights(n_u, gamma_u, m, cap_u))
-    cdf_v = np.cumsum(powerlaw_weights(n_v, gamma_v, m, cap_v))
-    keys = np.zeros(0, dtype=np.int64)
-    drawn = 0
-    for _ in range(200):
-        need = m - keys.shape[0]
-        if need <= 0:
-            break
-        k = int(need * 1.25) + 64
-        uu = _sample_index(cdf_u, uniform01(seed, 1, k, drawn))
-        vv = _sample_index(cdf_v, uniform01(seed, 2, k, drawn))
-        drawn += k
-        allk = np.concatenate([keys, uu * n_v + vv])
-        _, first = np.unique(allk, return_index=True)
-        keys = allk[np.sort(first)]
-    if keys.shape[0] < m:
+    u = np.empty(m, dtype=np.int64)
+    v = np.empty(m, dtype=np.int64)
+    rc = _c().synth_chung_lu(seed & 0xFFFFFFFFFFFFFFFF, n_u, n_v, m, float(gamma_u), float(gamma_v),
+                             float(cap_u), float(cap_v), u.ctypes.data, v.ctypes.data)
+    if rc == -2:
         raise RuntimeError("could not draw enough distinct edges")
-    keys = keys[:m]
-    u = keys // n_v
-    v = keys % n_v
-    perm_u = np.argsort(random_u64(seed, 3, n_u), kind="stable")
-    perm_v = np.argsort(random_u64(seed, 4, n_v), kind="stable")
-    return perm_u[u], perm_v[v]
+    if rc != 0:
+        raise MemoryError("sampler allocation failed")
+    return u, v
 
 
 def faction_signs(seed, u, v, n_u, n_v, flip, p_plus=0.5):
@@ -260,3 +262,12 @@ def tiny_random(seed: int, n_u: int, n_v: int, density: float, neg: float) -> Si
     keep = r < density
     sign = np.where(s < neg, -1, 1).astype(np.int8)
     return from_edges(n_u, n_v, uu[keep], vv[keep], sign[keep], f"tiny-{seed}")
+
+
+def batch_graphs(seed: int, count: int, m_lo: float = 500, m_hi: float = 500_000,
+                 threads: int = 0):
+    """Graphs 0..count-1 of a batch, generated on host threads (the C sampler
+    releases the interpreter lock)."""
+    threads = threads or min(32, os.cpu_count() or 1)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(lambda i: batch_graph(seed, i, m_lo, m_hi), range(count)))
