@@ -169,6 +169,114 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ batch / serve legs
+
+def batch_leg(sbc, torch, args):
+    """Graphs/s for B independent graphs (the 10,000-graph batch recipe,
+    first B graphs): plain one-count-per-graph path, one batched count
+    (sbc_count_batch) and a planned batch replayed from a CUDA graph."""
+    import sbc_synth
+
+    t0 = time.perf_counter()
+    gs = sbc_synth.batch_graphs(4, args.batch_graphs)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hs = [sbc.graph_from_synth(g) for g in gs]
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    edges = sum(g.m for g in gs)
+    p, q = 3, 3
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            res = fn()
+        torch.cuda.synchronize()
+        return res, (time.perf_counter() - t) / reps
+
+    plain, t_plain = timed(lambda: [sbc.sbc_count(h, p, q) for h in hs], 1)
+    batched, t_batch = timed(lambda: sbc.sbc_count_batch(hs, p, q), 3)
+    with sbc.Batch(hs, p, q) as b:
+        b.run()
+        replay, t_replay = timed(b.run, 5)
+    assert plain == batched == replay
+    for h in hs:
+        h.close()
+    n = len(gs)
+    return {"graphs": n, "edges": int(edges), "pq": "(3,3)", "generate_s": t_gen,
+            "create_s": t_create, "plain_graphs_per_s": n / t_plain,
+            "batched_graphs_per_s": n / t_batch, "replay_graphs_per_s": n / t_replay,
+            "batched_vs_plain": t_plain / t_batch, "replay_vs_plain": t_plain / t_replay,
+            "total_count": sum(plain)}
+
+
+def serve_leg(sbc, torch, args):
+    """Poisson-arriving requests (graph, p, q) on resident graphs: p50/p99
+    latency and throughput of the server versus one-at-a-time serving of the
+    same arrivals (a FIFO queue over each request's measured standalone time)."""
+    import threading
+
+    import sbc_synth
+
+    gs = sbc_synth.batch_graphs(5, args.serve_graphs, 1e3, args.serve_max_edges)
+    hs = [sbc.graph_from_synth(g) for g in gs]
+    pqs = [(3, 3), (3, 4), (4, 4)]
+    rng = np.random.default_rng(5)
+    reqs = [(int(rng.integers(len(hs))), pqs[int(rng.integers(3))]) for _ in range(args.serve_requests)]
+    # standalone service times (one request at a time, warmed)
+    service = {}
+    for g, pq in set(reqs):
+        sbc.sbc_count(hs[g], *pq)
+    for g, pq in set(reqs):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        service[(g, pq)] = sbc.sbc_count(hs[g], *pq)
+        service[(g, pq)] = (service[(g, pq)], time.perf_counter() - t)
+    out = []
+    with sbc.Server(mem_budget_bytes=int(args.serve_budget_gb * 2**30)) as srv:
+        gids = [srv.add_graph(h) for h in hs]
+        for rate in args.serve_rates:
+            arr = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+            # one at a time: Lindley recursion over measured service times
+            fin, lat1 = 0.0, []
+            for (g, pq), a in zip(reqs, arr):
+                start = max(a, fin)
+                fin = start + service[(g, pq)][1]
+                lat1.append(fin - a)
+            span1 = fin - arr[0]
+            srv.reset_stats()
+            tickets = [None] * len(reqs)
+            t_base = time.perf_counter()
+
+            def client():
+                for i, ((g, pq), a) in enumerate(zip(reqs, arr)):
+                    dt = t_base + a - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    tickets[i] = srv.submit(gids[g], *pq)
+
+            th = threading.Thread(target=client)
+            th.start()
+            th.join()
+            lat = []
+            for i, (g, pq) in enumerate(reqs):
+                c, l = srv.wait(tickets[i])
+                assert c == service[(g, pq)][0]  # same count alone and in the mix
+                lat.append(l)
+            st = srv.stats()
+            out.append({"rate_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                        "throughput_rps": st["throughput_rps"], "jobs": st["jobs"],
+                        "fused_requests": st["fused_requests"],
+                        "one_at_a_time": {"p50_ms": 1e3 * float(np.percentile(lat1, 50)),
+                                          "p99_ms": 1e3 * float(np.percentile(lat1, 99)),
+                                          "throughput_rps": len(reqs) / span1}})
+    for h in hs:
+        h.close()
+    return {"graphs": len(gs), "edges": int(sum(g.m for g in gs)), "requests": len(reqs),
+            "pq": "(3,3)|(3,4)|(4,4) uniform", "budget_gb": args.serve_budget_gb, "rates": out}
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_ours(args):
@@ -321,6 +429,12 @@ def run_ours(args):
                "sample": f"(3,3) on a seeded random {args.cpu_frac:.1%} sample of U anchors "
                          f"({na} anchors, {tup} tuples, {dt:.1f} s)"}
 
+    batch = serve = None
+    if rank == 0 and ws == 1 and args.batch_graphs > 0:
+        batch = batch_leg(sbc, torch, args)
+    if rank == 0 and ws == 1 and args.serve_requests > 0:
+        serve = serve_leg(sbc, torch, args)
+
     if rank == 0:
         s0 = per_step_stats[0]
         line = {
@@ -341,6 +455,7 @@ def run_ours(args):
             "roofline": roof, "peak_source": peak_kind,
             "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
             "cpu_baseline": cpu,
+            "batch": batch, "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -356,6 +471,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--batch-graphs", type=int, default=1000,
+                    help="graphs of the batch leg (0 skips it; the full batch is 10000)")
+    ap.add_argument("--serve-graphs", type=int, default=100)
+    ap.add_argument("--serve-max-edges", type=float, default=1e5)
+    ap.add_argument("--serve-requests", type=int, default=2000, help="0 skips the serving leg")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
+    ap.add_argument("--serve-budget-gb", type=float, default=80.0)
     ap.add_argument("--pq", action="append", default=None,
                     help="p,q pair to count (repeatable); default 3,3 and 4,4")
     ap.add_argument("--cpu-frac", type=float, default=0.10,

@@ -205,6 +205,52 @@ sbc_status sbc_batch_run(sbc_batch *b, sbc_u128 *out, void *stream);
 sbc_status sbc_batch_destroy(sbc_batch *b);
 
 /*
+ * Serving. A server answers count requests (graph, p, q) on resident graphs
+ * as they arrive. A scheduler thread forms jobs for a set of device lanes
+ * (one stream and worker thread each): requests on small graphs that wait
+ * together with the same (p, q) are fused into one batched count
+ * (sbc_count_batch semantics), requests on large graphs run alone; a job
+ * starts when a lane is free and the estimated device bytes of the jobs in
+ * flight plus its own stay within mem_budget_bytes (a job larger than the
+ * budget runs when nothing else does). Requests that arrive while others
+ * run are admitted as lanes and memory free up, and jobs on different lanes
+ * overlap on the device. Results are exact and never cached across requests.
+ * Graphs must stay alive and unchanged while the server uses them.
+ */
+typedef struct {
+    uint64_t mem_budget_bytes; /* device bytes for jobs in flight; 0 = 80% of free memory */
+    int32_t lanes;             /* concurrent device lanes; 0 = 4 */
+    int32_t max_batch;         /* most requests fused into one job; 0 = 64 */
+    int64_t small_edges;       /* graphs with at most this many edges are fused; 0 = 200000 */
+} sbc_server_opts;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t jobs;                /* counts dispatched to lanes */
+    uint64_t fused_requests;      /* requests that ran inside a multi-request job */
+    uint64_t peak_admitted_bytes; /* largest estimated footprint in flight */
+    uint64_t mem_budget_bytes;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* latency from submit to completion */
+    double throughput_rps;        /* completed / (last completion - first submit) */
+} sbc_server_stats_t;
+
+sbc_status sbc_server_create(const sbc_server_opts *opts, sbc_server **out);
+/* Register a resident graph; *gid identifies it in requests. */
+sbc_status sbc_server_add_graph(sbc_server *s, const sbc_graph *g, uint32_t *gid);
+/* Queue a request (thread-safe, returns at once); *ticket identifies it. */
+sbc_status sbc_server_submit(sbc_server *s, uint32_t gid, int p, int q, uint64_t *ticket);
+/* Wait for a request (timeout_us < 0: no limit; SBC_E_TIMEOUT when it runs
+ * out, the request stays pending). On return the ticket is released; the
+ * request's own status is returned (its count in *out, submit-to-finish time
+ * in *latency_s). */
+sbc_status sbc_server_wait(sbc_server *s, uint64_t ticket, int64_t timeout_us, sbc_u128 *out,
+                           double *latency_s);
+sbc_status sbc_server_stats(sbc_server *s, sbc_server_stats_t *out);
+sbc_status sbc_server_reset_stats(sbc_server *s);
+/* Stop the server: jobs already on a lane finish; waiting requests are dropped. */
+sbc_status sbc_server_destroy(sbc_server *s);
+
+/*
  * sbc_count_csr without any device allocation, for callers that cannot call
  * cudaMalloc (a fixed device-memory plan, a loop that must not enter the
  * allocator). No counterpart in the paper: same arguments and result as

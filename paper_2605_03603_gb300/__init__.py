@@ -20,7 +20,7 @@ from . import build as _build
 __all__ = [
     "SbcError", "Graph", "sbc_graph_create", "sbc_graph_destroy", "sbc_graph_info",
     "sbc_count", "sbc_count_ex", "sbc_count_csr", "sbc_last_error", "sbc_version",
-    "sbc_launch_count", "sbc_count_csr_noalloc", "sbc_count_batch", "Batch",
+    "sbc_launch_count", "sbc_count_csr_noalloc", "sbc_count_batch", "Batch", "Server",
     "lib", "LIB_PATH",
 ]
 
@@ -116,6 +116,31 @@ _declare("sbc_batch_create", ctypes.c_int,
          [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp), _vp])
 _declare("sbc_batch_run", ctypes.c_int, [_vp, ctypes.POINTER(U128), _vp])
 _declare("sbc_batch_destroy", ctypes.c_int, [_vp])
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("lanes", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("small_edges", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("jobs", ctypes.c_uint64),
+                ("fused_requests", ctypes.c_uint64), ("peak_admitted_bytes", ctypes.c_uint64),
+                ("mem_budget_bytes", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("throughput_rps", ctypes.c_double)]
+
+
+_declare("sbc_server_create", ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)])
+_declare("sbc_server_add_graph", ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_uint32)])
+_declare("sbc_server_submit", ctypes.c_int,
+         [_vp, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)])
+_declare("sbc_server_wait", ctypes.c_int,
+         [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(U128), ctypes.POINTER(ctypes.c_double)])
+_declare("sbc_server_stats", ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)])
+_declare("sbc_server_reset_stats", ctypes.c_int, [_vp])
+_declare("sbc_server_destroy", ctypes.c_int, [_vp])
 _declare("sbc_count_csr_noalloc", ctypes.c_int,
          [_i64, _i64, _i64, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
           ctypes.POINTER(U128), _vp])
@@ -351,6 +376,63 @@ class Batch:
     def close(self):
         if self.handle:
             _check(lib.sbc_batch_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request server over resident graphs (sbc_server_*): submit() queues a
+    count and returns a ticket at once; wait() returns (count, latency_s)."""
+
+    def __init__(self, mem_budget_bytes: int = 0, lanes: int = 0, max_batch: int = 0,
+                 small_edges: int = 0):
+        o = ServerOpts(mem_budget_bytes, lanes, max_batch, small_edges)
+        h = _vp()
+        _check(lib.sbc_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h.value
+        self.graphs = []
+
+    def add_graph(self, g: Graph) -> int:
+        gid = ctypes.c_uint32()
+        _check(lib.sbc_server_add_graph(self.handle, g.handle, ctypes.byref(gid)))
+        self.graphs.append(g)
+        return int(gid.value)
+
+    def submit(self, gid: int, p: int, q: int) -> int:
+        t = ctypes.c_uint64()
+        _check(lib.sbc_server_submit(self.handle, gid, p, q, ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        out = U128()
+        lat = ctypes.c_double()
+        _check(lib.sbc_server_wait(self.handle, ticket, timeout_us, ctypes.byref(out),
+                                   ctypes.byref(lat)))
+        return out.value(), float(lat.value)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib.sbc_server_stats(self.handle, ctypes.byref(st)))
+        return {f: (float(getattr(st, f)) if t is ctypes.c_double else int(getattr(st, f)))
+                for f, t in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(lib.sbc_server_reset_stats(self.handle))
+
+    def close(self):
+        if self.handle:
+            _check(lib.sbc_server_destroy(self.handle))
             self.handle = None
 
     def __enter__(self):

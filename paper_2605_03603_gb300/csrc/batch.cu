@@ -259,6 +259,10 @@ sbc_batch *batch_create(const sbc_graph *const *gs_in, size_t n, int p, int q, b
     return b.release();
 }
 
+const sbc_u128 *batch_first(const sbc_batch *b) { return b->first.data(); }
+
+void batch_destroy(sbc_batch *b) { delete b; }
+
 void batch_run(sbc_batch *b, sbc_u128 *out, cudaStream_t s) {
     int cur = 0;
     SBC_CUDA(cudaGetDevice(&cur));

@@ -2134,12 +2134,19 @@ void set_tuple_attr() {
                                   (int)PB_SMEM));
 }
 
-// Opt every large-shared-memory kernel in once per process (per device).
+// Opt every large-shared-memory kernel in, and load the binomial limits,
+// once per device.
 void ensure_kernel_attrs() {
     static std::mutex mu;
-    static bool done = false;
+    static bool done[64] = {};
     std::lock_guard<std::mutex> lock(mu);
-    if (done) return;
+    int dev = 0;
+    SBC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(SBC_E_UNSUPPORTED, "device ordinal %d out of range", dev);
+    if (done[dev]) return;
+    unsigned long long lim[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 2; i <= 8; i++) lim[i] = binom64_limit(i);
+    SBC_CUDA(cudaMemcpyToSymbol(c_binom64_max, lim, sizeof(lim)));
     SBC_CUDA(cudaFuncSetAttribute(k_twohop_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PS_SMEM));
     SBC_CUDA(cudaFuncSetAttribute(k_twohop_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PS_SMEM));
     SBC_CUDA(cudaFuncSetAttribute(k_twohop_large<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL_SMEM));
@@ -2151,7 +2158,7 @@ void ensure_kernel_attrs() {
     set_tuple_attr<5>();
     set_tuple_attr<6>();
     set_tuple_attr<7>();
-    done = true;
+    done[dev] = true;
 }
 
 template <int R>
@@ -2251,9 +2258,6 @@ struct CountRun {
         const int B = 256;
         const int l = spec.l;
         R = spec.k - 1;
-        unsigned long long lim[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int i = 2; i <= 8; i++) lim[i] = binom64_limit(i);
-        SBC_CUDA(cudaMemcpyToSymbolAsync(c_binom64_max, lim, sizeof(lim), 0, cudaMemcpyHostToDevice, s));
         cnt.alloc(1, s);
         SBC_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(Counters), s));
         A_bit.alloc(nnz, s);
