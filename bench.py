@@ -102,10 +102,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+WORKLOADS = {"plain-200k-100k-2M": "plain_medium", "plain-50k-25k-500k": "plain_quarter",
+             "plain-2k-1.5k-20k": "plain_small", "plain-5M-1M-60M": "plain_large"}
+
+
 def load_workload():
     import sbc_synth
 
-    return sbc_synth.plain_medium()
+    return getattr(sbc_synth, WORKLOADS[WORKLOAD])()
 
 
 def measured_peaks():
@@ -464,6 +468,7 @@ def run_ours(args):
 
 
 def main():
+    global PQ, WORKLOAD
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -478,6 +483,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000, help="0 skips the serving leg")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
+                    help="graph to count (default: the 200k x 100k x 2M workload)")
     ap.add_argument("--pq", action="append", default=None,
                     help="p,q pair to count (repeatable); default 3,3 and 4,4")
     ap.add_argument("--cpu-frac", type=float, default=0.10,
@@ -485,7 +492,7 @@ def main():
     ap.add_argument("--ref-frac", type=float, default=0.02,
                     help="anchor sample fraction per step for --impl reference")
     args = ap.parse_args()
-    global PQ
+    WORKLOAD = args.workload
     if args.pq:
         PQ = [tuple(int(x) for x in pq.split(",")) for pq in args.pq]
     if args.impl == "reference":

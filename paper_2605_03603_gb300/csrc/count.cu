@@ -122,9 +122,10 @@ __device__ __forceinline__ unsigned long long binom_u64(unsigned long long x) {
     return r;
 }
 
-// acc += binom(x, l), exact. Sets CERR_OVERFLOW if the term needs > 128 bits.
-__device__ __noinline__ void binom_add_slow(U128 &acc, unsigned long long x, int l,
-                                            unsigned *err) {
+// binom(x, l) in 128 bits, exact (returned by value so that callers'
+// accumulators stay in registers). Sets CERR_OVERFLOW if it needs more.
+__device__ __noinline__ U128 binom_slow(unsigned long long x, int l, unsigned *err) {
+    U128 t;
     unsigned long long lo = 1, hi = 0;
     for (int i = 1; i <= l; i++) {
         unsigned long long f = x - l + i;
@@ -133,19 +134,18 @@ __device__ __noinline__ void binom_add_slow(U128 &acc, unsigned long long x, int
         div_u128_small(lo, hi, (unsigned)i / g);
         if (!mul_u128_u64(lo, hi, f / g)) {
             atomicOr(err, CERR_OVERFLOW);
-            return;
+            return t;
         }
     }
-    U128 t;
     t.lo = lo;
     t.hi = hi;
-    acc.add(t);
+    return t;
 }
 
 __device__ __forceinline__ void binom_add(U128 &acc, unsigned x, int l, unsigned *err) {
     if ((int)x < l) return;
     if (x > c_binom64_max[l]) {
-        binom_add_slow(acc, x, l, err);
+        acc.add(binom_slow(x, l, err));
         return;
     }
     unsigned long long v;
@@ -862,7 +862,7 @@ constexpr uint32_t POS_ITEM = 0xFFFFFFFFu;
 constexpr int POS_MAX_WORDS = 128;  // candidate words of a position-side mask (4 per lane)
 
 constexpr int ROWS_MAX = 1024;
-constexpr int PB_SMEM_WORDS_PLAN = 16384;  // staged words of the tuple kernel (PB_SMEM_WORDS)
+constexpr int PB_SMEM_WORDS_PLAN = 24576;  // staged words of the tuple kernel (PB_SMEM_WORDS)
 
 struct ItemArgs {
     const uint32_t *ncand, *npaper, *dprime;
@@ -1099,7 +1099,7 @@ __global__ void k_items(ItemArgs a) {
 
 constexpr int PB_THREADS = 256;
 constexpr int PB_WARPS = PB_THREADS / 32;
-constexpr int PB_SMEM_WORDS = PB_SMEM_WORDS_PLAN;  // 64 KB of staged words
+constexpr int PB_SMEM_WORDS = PB_SMEM_WORDS_PLAN;  // 96 KB of staged words
 constexpr size_t PB_SMEM = PB_SMEM_WORDS * 4;
 constexpr int SCRATCH_SLOTS = 7;  // per-warp mask slots for wide anchors (>= max(R, 6))
 
@@ -1746,7 +1746,7 @@ __device__ __forceinline__ void binom_add_r(U128 &acc, unsigned long long x, uns
         acc.add(x);
     } else {
         if (x > c_binom64_max[R]) {
-            binom_add_slow(acc, x, R, err);
+            acc.add(binom_slow(x, R, err));
             return;
         }
         acc.add(binom_u64<R>(x));
@@ -1912,7 +1912,7 @@ __device__ void pos_row(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q
 }
 
 template <int R>
-__global__ void __launch_bounds__(PB_THREADS, 3) k_tuples(TupleArgs a) {
+__global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ int s_item;
     __shared__ uint32_t s_unit, s_total;

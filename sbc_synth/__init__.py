@@ -214,6 +214,13 @@ def plain_medium(seed: int = 2) -> SignedBipartite:
                            p_plus=_PI_75, name="plain-200k-100k-2M")
 
 
+def plain_quarter(seed: int = 2) -> SignedBipartite:
+    """The medium workload's shape at a quarter of its size: 50,000 x 25,000,
+    500,000 edges (profiling case)."""
+    return chung_lu_signed(seed, 50_000, 25_000, 500_000, 2.0, 2.3, 0.15,
+                           p_plus=_PI_75, name="plain-50k-25k-500k")
+
+
 def plain_large(seed: int = 3) -> SignedBipartite:
     """5,000,000 x 1,000,000, 60,000,000 edges, exponents 2.4 (U) / 1.9 (V),
     V hubs capped at 50,000 expected degree; 4 planted factions, flip 0.2."""
