@@ -121,6 +121,31 @@ sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
 #define SBC_COUNT_POSITION_SIDE (1 << 2)  /* enumerate position subsets wherever they fit
                                              (default: the cheaper side per anchor) */
 
+/*
+ * Launch parameters of the counting kernels: the search space of the
+ * autotuner (sbc_autotune). They change how the work is spread over the GPU,
+ * never the count. Zero in a field selects the built-in default.
+ *   small_wedges   anchors whose 2-hop visit (Algorithm 2's cnt loop) covers
+ *                  at most this many wedges take the warp-per-anchor 2-hop
+ *                  kernel; the others take a whole CTA of 16 warps each.
+ *                  1..512, default 512.
+ *   pos_node_cost  cost of one prefix node of the position-side enumeration
+ *                  relative to one word test of the candidate-side
+ *                  enumeration; each anchor takes the cheaper side, so a
+ *                  larger value favours the candidate (bitmap AND/POPC over
+ *                  candidate tuples) side. 1..2^20, default 6.
+ *   split_per_warp work items per warp of a full-GPU tuple launch: heavy
+ *                  anchors are split into items of about (estimated total
+ *                  cost) / (resident warps x split_per_warp). 1..64, default 4.
+ * SBC_E_INVAL for a field outside its range.
+ */
+typedef struct {
+    int32_t small_wedges;
+    int32_t pos_node_cost;
+    int32_t split_per_warp;
+    float ms; /* sbc_autotune: time of one count with the chosen parameters */
+} sbc_tune_t;
+
 typedef struct {
     int32_t anchor_side;  /* SBC_SIDE_AUTO, SBC_SIDE_U or SBC_SIDE_V */
     int32_t flags;        /* SBC_COUNT_* bits, 0 for a plain count */
@@ -130,6 +155,7 @@ typedef struct {
     /* first shard of anchors and number of shards: anchors with
      * (rank of the anchor) % shard_count == shard are counted. 0/0 or 0/1 = all. */
     int32_t shard, shard_count;
+    const sbc_tune_t *tune; /* launch parameters, or NULL for the defaults */
 } sbc_count_opts;
 
 typedef struct {
@@ -201,8 +227,27 @@ sbc_status sbc_count_batch(const sbc_graph *const *graphs, size_t n, int p, int 
  */
 sbc_status sbc_batch_create(const sbc_graph *const *graphs, size_t n, int p, int q,
                             sbc_batch **out, void *stream);
+/* sbc_batch_create with launch parameters (NULL: defaults), e.g. from sbc_autotune. */
+sbc_status sbc_batch_create_ex(const sbc_graph *const *graphs, size_t n, int p, int q,
+                               const sbc_tune_t *tune, sbc_batch **out, void *stream);
 sbc_status sbc_batch_run(sbc_batch *b, sbc_u128 *out, void *stream);
 sbc_status sbc_batch_destroy(sbc_batch *b);
+
+/*
+ * Autotuner (the paper has no counterpart: its algorithm has no launch
+ * parameters). Times the counting kernels of the batch `graphs` (n >= 1; a
+ * single graph is a batch of one) for (p, q) under candidate launch
+ * parameters and writes the fastest to *out (out->ms = its time per count).
+ * The search is coordinate descent from the defaults over split_per_warp
+ * {1, 2, 4, 8, 16}, small_wedges {64, 128, 256, 512} and pos_node_cost
+ * {2, 4, 6, 10, 16, 64, 2^20}; each candidate is planned once and its
+ * counting kernels timed (best of `reps`, 0 = 3) with CUDA events on
+ * `stream`. Every candidate must produce the same counts, or the call fails
+ * with SBC_E_CUDA. Synchronises `stream`; allocates and frees device memory
+ * like sbc_batch_create.
+ */
+sbc_status sbc_autotune(const sbc_graph *const *graphs, size_t n, int p, int q, int32_t reps,
+                        sbc_tune_t *out, void *stream);
 
 /*
  * Serving. A server answers count requests (graph, p, q) on resident graphs

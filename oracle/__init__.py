@@ -51,7 +51,7 @@ def _declare(lib):
     lib.sbc_oracle_count.argtypes = [
         ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_void_p,
-        ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
     ]
     lib.sbc_oracle_binom.restype = ctypes.c_int
     lib.sbc_oracle_binom.argtypes = [ctypes.c_int64, ctypes.c_int, u64p]
@@ -89,7 +89,8 @@ def _u128(lo, hi) -> int:
 
 
 def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
-          per_anchor: bool = False, with_tuples: bool = False, lib=None, anchors=None):
+          per_anchor: bool = False, with_tuples: bool = False, lib=None, anchors=None,
+          max_subsets: int = 0, skipped=None):
     """Balanced (p,q)-bicliques of `g` (p from U, q from V) by Algorithm 2.
 
     side: anchor partition S (0 = U with tuple size p, 1 = V with tuple size
@@ -97,7 +98,9 @@ def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
     Returns the count (int); with per_anchor, also a list of each anchor's
     contribution (indexed by vertex id of S); with with_tuples, also the
     number of (|S-tuple|-1)-subsets of C enumerated. anchors: optional
-    iterable of S-vertex ids; only those anchors are processed.
+    iterable of S-vertex ids; only those anchors are processed. max_subsets
+    (tests only): anchors with more subsets to enumerate are left out; their
+    ids are added to the set `skipped` if given.
     """
     lib = _load() if lib is None else lib
     if side is None:
@@ -109,6 +112,7 @@ def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
     tup = (ctypes.c_uint64 * 2)()
     n_s = g.n_u if side == 0 else g.n_v
     anc = np.zeros(2 * max(n_s, 1), dtype=np.uint64) if per_anchor else None
+    skip = np.zeros(max(n_s, 1), dtype=np.uint8) if max_subsets else None
     mask = None
     if anchors is not None:
         mask = np.zeros(max(n_s, 1), dtype=np.uint8)
@@ -116,8 +120,11 @@ def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
     rc = lib.sbc_oracle_count(
         g.n_u, g.n_v, off.ctypes.data, col.ctypes.data, sgn.ctypes.data, p, q, side, threads,
         out, anc.ctypes.data if anc is not None else None, ctypes.addressof(tup),
-        mask.ctypes.data if mask is not None else None,
+        mask.ctypes.data if mask is not None else None, max_subsets,
+        skip.ctypes.data if skip is not None else None,
     )
+    if skip is not None and skipped is not None:
+        skipped.update(np.nonzero(skip)[0].tolist())
     if rc == 1:
         raise OverflowError("balanced biclique count term exceeds 128 bits")
     if rc != 0:

@@ -212,8 +212,8 @@ typedef struct {
  * p = tuple size on S, q = size on the other side.
  */
 static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
-                const uint8_t *anchor_mask, uint64_t out[2], uint64_t *anchor_out,
-                uint64_t *tuples_out, int *ovf_out) {
+                const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped,
+                uint64_t out[2], uint64_t *anchor_out, uint64_t *tuples_out, int *ovf_out) {
     int64_t nS = s->n;
     int ovf = 0;
     int nt = 1;
@@ -289,6 +289,14 @@ static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
                 if (w.cnt[w.touched[i]] >= q) w.cand[nc++] = w.touched[i];
 #endif
             for (int64_t i = 0; i < nt_touch; i++) w.cnt[w.touched[i]] = 0;
+            if (nc >= p - 1 && max_subsets) {
+                /* test option: leave out anchors with too many subsets */
+                int dummy = 0;
+                if (binom_u128(nc, p - 1, &dummy) > (u128)max_subsets || dummy) {
+                    if (skipped) skipped[u] = 1;
+                    nc = 0;
+                }
+            }
             if (nc >= p - 1) {
                 /* w_1 < ... < w_{p-1}: order C by vertex id */
                 qsort(w.cand, (size_t)nc, sizeof(int32_t), cmp_i32);
@@ -429,13 +437,15 @@ static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
  * tuples_out (optional): number of (p-1)-subsets enumerated, {lo, hi}.
  * anchor_mask (optional): one byte per vertex of S; only anchors with a
  * non-zero byte are processed (the total then covers those anchors only).
+ * max_subsets (test option, 0 = none): anchors whose (p-1)-subsets of C
+ * number more are left out and flagged in `skipped` (one byte per vertex).
  * Returns 0, -1 on allocation failure, -2 on bad arguments, 1 on overflow.
  */
 int sbc_oracle_count(int64_t n_u, int64_t n_v, const int64_t *off,
                      const int32_t *col, const int8_t *sgn, int p_u, int q_v,
                      int anchor_side, int nthreads, uint64_t out[2],
                      uint64_t *anchor_out, uint64_t *tuples_out,
-                     const uint8_t *anchor_mask) {
+                     const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped) {
     if (p_u < 2 || q_v < 2 || p_u > 16 || q_v > 16 || n_u < 0 || n_v < 0) return -2;
     side_t su, sv;
     memset(&su, 0, sizeof(su));
@@ -447,9 +457,11 @@ int sbc_oracle_count(int64_t n_u, int64_t n_v, const int64_t *off,
     }
     int ovf = 0, rc;
     if (anchor_side == 0)
-        rc = bbvp(&su, &sv, p_u, q_v, nthreads, anchor_mask, out, anchor_out, tuples_out, &ovf);
+        rc = bbvp(&su, &sv, p_u, q_v, nthreads, anchor_mask, max_subsets, skipped, out,
+                  anchor_out, tuples_out, &ovf);
     else
-        rc = bbvp(&sv, &su, q_v, p_u, nthreads, anchor_mask, out, anchor_out, tuples_out, &ovf);
+        rc = bbvp(&sv, &su, q_v, p_u, nthreads, anchor_mask, max_subsets, skipped, out,
+                  anchor_out, tuples_out, &ovf);
     free_side(&su);
     free_side(&sv);
     if (rc) return rc;

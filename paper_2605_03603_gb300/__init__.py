@@ -60,10 +60,29 @@ class GraphInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64)]
 
 
+class Tune(ctypes.Structure):
+    """sbc_tune_t: launch parameters of the counting kernels (0 = default)."""
+    _fields_ = [("small_wedges", ctypes.c_int32), ("pos_node_cost", ctypes.c_int32),
+                ("split_per_warp", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {"small_wedges": int(self.small_wedges), "pos_node_cost": int(self.pos_node_cost),
+                "split_per_warp": int(self.split_per_warp), "ms": float(self.ms)}
+
+
+def _tune(t) -> "Tune | None":
+    if t is None:
+        return None
+    if isinstance(t, Tune):
+        return t
+    return Tune(int(t.get("small_wedges", 0)), int(t.get("pos_node_cost", 0)),
+                int(t.get("split_per_warp", 0)), 0.0)
+
+
 class CountOpts(ctypes.Structure):
     _fields_ = [("anchor_side", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("per_anchor", ctypes.c_void_p), ("shard", ctypes.c_int32),
-                ("shard_count", ctypes.c_int32)]
+                ("shard_count", ctypes.c_int32), ("tune", ctypes.POINTER(Tune))]
 
 
 class CountStats(ctypes.Structure):
@@ -114,6 +133,12 @@ _declare("sbc_count_batch", ctypes.c_int,
          [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(U128), _vp])
 _declare("sbc_batch_create", ctypes.c_int,
          [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp), _vp])
+_declare("sbc_batch_create_ex", ctypes.c_int,
+         [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tune),
+          ctypes.POINTER(_vp), _vp])
+_declare("sbc_autotune", ctypes.c_int,
+         [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int32,
+          ctypes.POINTER(Tune), _vp])
 _declare("sbc_batch_run", ctypes.c_int, [_vp, ctypes.POINTER(U128), _vp])
 _declare("sbc_batch_destroy", ctypes.c_int, [_vp])
 
@@ -276,10 +301,15 @@ def sbc_count(g: Graph, p: int, q: int, stream=None) -> int:
 
 def sbc_count_ex(g: Graph, p: int, q: int, anchor_side: int = SBC_SIDE_AUTO,
                  per_anchor: bool = False, paper_tuples: bool = False, shard: int = 0,
-                 shard_count: int = 0, method: str = "auto", stream=None):
+                 shard_count: int = 0, method: str = "auto", tune=None, stream=None):
     """sbc_count_ex: returns (count, stats dict, per-anchor list or None).
-    method: "auto" (cheaper side per anchor), "candidate" or "position"."""
+    method: "auto" (cheaper side per anchor), "candidate" or "position".
+    tune: launch parameters (a dict with sbc_tune_t's fields, e.g. from
+    sbc_autotune, or None for the defaults)."""
     opts = CountOpts()
+    t = _tune(tune)
+    if t is not None:
+        opts.tune = ctypes.pointer(t)
     opts.anchor_side = anchor_side
     opts.flags = (SBC_COUNT_PAPER_TUPLES if paper_tuples else 0) | {
         "auto": 0, "candidate": SBC_COUNT_CANDIDATE_SIDE, "position": SBC_COUNT_POSITION_SIDE}[method]
@@ -356,15 +386,28 @@ def sbc_count_batch(graphs, p: int, q: int, stream=None) -> list:
     return [out[i].value() for i in range(len(graphs))]
 
 
+def sbc_autotune(graphs, p: int, q: int, reps: int = 0, stream=None) -> dict:
+    """sbc_autotune: the fastest launch parameters for counting this batch of
+    graphs (one graph is a batch of one); returns sbc_tune_t's fields as a
+    dict, with "ms" the time of one count under them."""
+    out = Tune()
+    gl = list(graphs)
+    _check(lib.sbc_autotune(_handles(gl), len(gl), p, q, reps, ctypes.byref(out),
+                            _stream_ptr(stream)))
+    return out.as_dict()
+
+
 class Batch:
     """A planned batch (sbc_batch_create); run() replays its counting kernels
     from a captured CUDA graph."""
 
-    def __init__(self, graphs, p: int, q: int, stream=None):
+    def __init__(self, graphs, p: int, q: int, tune=None, stream=None):
         self.graphs = list(graphs)  # keep the graphs alive
         h = _vp()
-        _check(lib.sbc_batch_create(_handles(self.graphs), len(self.graphs), p, q, ctypes.byref(h),
-                                    _stream_ptr(stream)))
+        t = _tune(tune)
+        _check(lib.sbc_batch_create_ex(_handles(self.graphs), len(self.graphs), p, q,
+                                       ctypes.byref(t) if t is not None else None,
+                                       ctypes.byref(h), _stream_ptr(stream)))
         self.handle = h.value
 
     def run(self, stream=None) -> list:

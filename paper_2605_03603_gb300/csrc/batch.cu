@@ -81,6 +81,7 @@ struct BatchGroup {
     int64_t nnz = 0;
     DevBuf<int64_t> x0;        // first rank of each member, n+1
     DevBuf<unsigned long long> totals;  // 2 words per member
+    CountSpec spec;            // defaults plus the batch's launch parameters
     CountRun *run = nullptr;
     ~BatchGroup() {
         if (run) countrun_destroy(run);
@@ -202,7 +203,7 @@ void read_totals(sbc_batch *b, sbc_u128 *out, cudaStream_t s) {
 }  // namespace
 
 sbc_batch *batch_create(const sbc_graph *const *gs_in, size_t n, int p, int q, bool capture,
-                        cudaStream_t s) {
+                        const sbc_tune_t *tune, cudaStream_t s) {
     if (p < 2 || q < 2 || p > 8 || q > 8) fail(SBC_E_INVAL, "p and q must be in [2, 8], got (%d, %d)", p, q);
     if (n > 0 && !gs_in) fail(SBC_E_INVAL, "graphs is NULL");
     std::unique_ptr<sbc_batch> b(new sbc_batch());
@@ -234,14 +235,17 @@ sbc_batch *batch_create(const sbc_graph *const *gs_in, size_t n, int p, int q, b
         spec.k = (p == q || sd == 0) ? p : q;
         spec.l = (p == q || sd == 0) ? q : p;
         spec.pos_unit = pos_node_cost_setting();
+        apply_tune(spec, tune);
         spec.per_graph = bg->totals.ptr;
         spec.graph_x0 = bg->x0.ptr;
         spec.n_graphs = (int)bg->members.size();
+        bg->spec = spec;
         bg->run = countrun_create(bg->uni, bg->nnz, spec, s, nullptr);
         b->groups.push_back(bg.release());
     }
     b->first.assign(n, sbc_u128{0, 0});
     read_totals(b.get(), b->first.data(), s);
+    for (auto *bg : b->groups) capture = capture && countrun_replayable(bg->run);
     if (capture) {
         SBC_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
         SBC_CUDA(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
@@ -272,9 +276,92 @@ void batch_run(sbc_batch *b, sbc_u128 *out, cudaStream_t s) {
     } else {
         for (auto *bg : b->groups) countrun_launch(bg->run, s);
     }
-    g_launches += 0;
     for (auto *bg : b->groups) countrun_collect(bg->run, s);
     read_totals(b, out, s);
+}
+
+namespace {
+
+bool same_counts(const std::vector<sbc_u128> &a, const std::vector<sbc_u128> &b) {
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); i++)
+        if (a[i].lo != b[i].lo || a[i].hi != b[i].hi) return false;
+    return true;
+}
+
+struct Events {
+    cudaEvent_t a = nullptr, b = nullptr;
+    Events() {
+        SBC_CUDA(cudaEventCreate(&a));
+        SBC_CUDA(cudaEventCreate(&b));
+    }
+    ~Events() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+}  // namespace
+
+// Coordinate descent over the launch parameters; every candidate is planned on
+// the same unions and its counting kernels are timed.
+void autotune(const sbc_graph *const *gs, size_t n, int p, int q, int reps, sbc_tune_t *out,
+              cudaStream_t s) {
+    if (n == 0) fail(SBC_E_INVAL, "autotune needs at least one graph");
+    if (reps < 0 || reps > 1000) fail(SBC_E_INVAL, "reps must be in [0, 1000], got %d", reps);
+    if (reps == 0) reps = 3;
+    std::unique_ptr<sbc_batch> b(batch_create(gs, n, p, q, false, nullptr, s));
+    const std::vector<sbc_u128> want = b->first;
+    std::vector<sbc_u128> got(n);
+    Events ev;
+    auto measure = [&](const sbc_tune_t &t) -> float {
+        for (auto *bg : b->groups) {
+            countrun_destroy(bg->run);
+            bg->run = nullptr;
+            CountSpec spec = bg->spec;
+            apply_tune(spec, &t);
+            bg->run = countrun_create(bg->uni, bg->nnz, spec, s, nullptr);
+        }
+        read_totals(b.get(), got.data(), s);
+        if (!same_counts(got, want))
+            fail(SBC_E_CUDA, "internal error: launch parameters (%d, %d, %d) changed a count",
+                 t.small_wedges, t.pos_node_cost, t.split_per_warp);
+        float best = 3.0e38f;
+        for (int r = 0; r < reps; r++) {
+            SBC_CUDA(cudaEventRecord(ev.a, s));
+            for (auto *bg : b->groups) countrun_launch(bg->run, s);
+            SBC_CUDA(cudaEventRecord(ev.b, s));
+            SBC_CUDA(cudaEventSynchronize(ev.b));
+            float ms = 0;
+            SBC_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+            best = std::min(best, ms);
+        }
+        for (auto *bg : b->groups) countrun_collect(bg->run, s);
+        read_totals(b.get(), got.data(), s);
+        if (!same_counts(got, want))
+            fail(SBC_E_CUDA, "internal error: a replay with launch parameters (%d, %d, %d) "
+                             "changed a count", t.small_wedges, t.pos_node_cost, t.split_per_warp);
+        return best;
+    };
+    sbc_tune_t cur{0, 0, 0, 0.0f};
+    cur.ms = measure(cur);
+    const int splits[] = {1, 2, 4, 8, 16};
+    const int smalls[] = {64, 128, 256, 512};
+    const int costs[] = {2, 4, 6, 10, 16, 64, 1 << 20};
+    auto sweep = [&](int32_t sbc_tune_t::*field, const int *vals, int nv) {
+        sbc_tune_t best = cur;
+        for (int i = 0; i < nv; i++) {
+            sbc_tune_t t = cur;
+            t.*field = vals[i];
+            t.ms = measure(t);
+            if (t.ms < best.ms) best = t;
+        }
+        cur = best;
+    };
+    sweep(&sbc_tune_t::split_per_warp, splits, 5);
+    sweep(&sbc_tune_t::small_wedges, smalls, 4);
+    sweep(&sbc_tune_t::pos_node_cost, costs, 7);
+    *out = cur;
 }
 
 }  // namespace sbc
@@ -301,7 +388,24 @@ sbc_status sbc_batch_create(const sbc_graph *const *graphs, size_t n, int p, int
     SBC_BATCH_TRY
     if (!out) fail(SBC_E_INVAL, "out is NULL");
     *out = nullptr;
-    *out = batch_create(graphs, n, p, q, true, (cudaStream_t)stream);
+    *out = batch_create(graphs, n, p, q, true, nullptr, (cudaStream_t)stream);
+    SBC_BATCH_END
+}
+
+sbc_status sbc_batch_create_ex(const sbc_graph *const *graphs, size_t n, int p, int q,
+                               const sbc_tune_t *tune, sbc_batch **out, void *stream) {
+    SBC_BATCH_TRY
+    if (!out) fail(SBC_E_INVAL, "out is NULL");
+    *out = nullptr;
+    *out = batch_create(graphs, n, p, q, true, tune, (cudaStream_t)stream);
+    SBC_BATCH_END
+}
+
+sbc_status sbc_autotune(const sbc_graph *const *graphs, size_t n, int p, int q, int32_t reps,
+                        sbc_tune_t *out, void *stream) {
+    SBC_BATCH_TRY
+    if (!out) fail(SBC_E_INVAL, "out is NULL");
+    autotune(graphs, n, p, q, reps, out, (cudaStream_t)stream);
     SBC_BATCH_END
 }
 
@@ -324,7 +428,7 @@ sbc_status sbc_count_batch(const sbc_graph *const *graphs, size_t n, int p, int 
                            void *stream) {
     SBC_BATCH_TRY
     if (!out && n) fail(SBC_E_INVAL, "out is NULL");
-    std::unique_ptr<sbc_batch> b(batch_create(graphs, n, p, q, false, (cudaStream_t)stream));
+    std::unique_ptr<sbc_batch> b(batch_create(graphs, n, p, q, false, nullptr, (cudaStream_t)stream));
     for (size_t i = 0; i < n; i++) out[i] = b->first[i];
     SBC_BATCH_END
 }

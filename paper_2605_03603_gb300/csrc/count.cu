@@ -315,6 +315,8 @@ struct TwohopArgs {
     Counters *cnt;
     unsigned long long *bucket;     // per-CTA bucket slots of the large-anchor kernel
     unsigned long long bucket_slot; // entries per slot
+    unsigned large_begin, large_end;  // order[] ranges of the two kernels
+    unsigned small_begin, small_end;
     int l;
 };
 
@@ -386,13 +388,12 @@ __global__ void __launch_bounds__(PS_THREADS) k_twohop_small(TwohopArgs a) {
         (unsigned long long *)(smem_raw + (size_t)PS_WARPS * PS_HS * 4 + (size_t)warp * PS_HS * 8);
     const int l = a.l;
     const uint32_t lt = (1u << lane) - 1u;
-    const unsigned n_big = a.cnt->n_big, n_act = a.cnt->n_active;
     unsigned long long wedges = 0;
     for (;;) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(&a.cnt->head_small, 1u);
-        item = __shfl_sync(FULL, item, 0) + n_big;
-        if (item >= n_act) break;
+        item = __shfl_sync(FULL, item, 0) + a.small_begin;
+        if (item >= a.small_end) break;
         const uint32_t r = a.order[item];
         const int64_t ebase = a.A_off[r];
         const int d = (int)(a.A_off[r + 1] - ebase);
@@ -606,7 +607,6 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
     __shared__ uint32_t s_bcnt[PL_MAXCLS];
     const int tid = threadIdx.x, lane = tid & 31;
     const int l = a.l;
-    const unsigned n_big = a.cnt->n_big;
     unsigned long long *bucket =
         a.bucket ? a.bucket + (size_t)blockIdx.x * a.bucket_slot : nullptr;
     unsigned long long wedges = 0;
@@ -644,11 +644,11 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
     };
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(&a.cnt->head_large, 1u);
+        if (tid == 0) s_item = a.large_begin + atomicAdd(&a.cnt->head_large, 1u);
         __syncthreads();
         const unsigned item = s_item;
         __syncthreads();
-        if (item >= n_big) break;
+        if (item >= a.large_end) break;
         const uint32_t r = a.order[item];
         const int64_t ebase = a.A_off[r];
         const int d = (int)(a.A_off[r + 1] - ebase);
@@ -838,6 +838,24 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
     if (tid == 0 && wedges) atomicAdd(&a.cnt->wedges, wedges);
 }
 
+// ------------------------------------------------------------------ groups
+
+// Candidate-mask words of the sorted anchors: gw[i] = words of order[i].
+__global__ void k_gather_words(const uint32_t *order, const int64_t *words_by_rank, int64_t n,
+                               int64_t *gw) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        gw[i] = i < n ? words_by_rank[order[i]] : 0;
+}
+
+// Pool offsets of one group of sorted anchors [a, b): offset from cum[a].
+__global__ void k_group_offsets(const uint32_t *order, const int64_t *cum, int64_t a, int64_t b,
+                                int64_t *pool_off) {
+    for (int64_t i = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b;
+         i += (int64_t)gridDim.x * blockDim.x)
+        pool_off[order[i]] = cum[i] - cum[a];
+}
+
 // ------------------------------------------------------------------ items
 
 // Saturating binom(n, k) in 64 bits (planning cost only).
@@ -866,7 +884,9 @@ constexpr int PB_SMEM_WORDS_PLAN = 24576;  // staged words of the tuple kernel (
 
 struct ItemArgs {
     const uint32_t *ncand, *npaper, *dprime;
-    int64_t nX;
+    const uint32_t *order;  // anchors of the group: order[begin .. begin + nX)
+    int64_t begin;
+    int64_t nX;             // anchors in the group
     int R, l;
     int method;  // 0: cheaper side per anchor, 1: candidate side, 2: position side where it fits
     unsigned long long pos_unit;  // cost of one position-side prefix node per candidate word-lane
@@ -951,8 +971,9 @@ __device__ __forceinline__ bool use_pos(uint32_t nc, uint32_t dp, int R, int l, 
 __global__ void k_anchor_cost(ItemArgs a) {
     U128 tp, to;
     unsigned long long cand = 0, cost = 0;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.nX;
-         r += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ix < a.nX;
+         ix += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = a.order[a.begin + ix];
         uint32_t nc = a.ncand[r];
         uint32_t W = (a.dprime[r] + 31) / 32;
         if (a.npaper) {
@@ -1003,12 +1024,13 @@ __global__ void k_anchor_cost(ItemArgs a) {
 // Split each anchor's tuple space into items. EMIT == false counts them.
 template <bool EMIT>
 __global__ void k_items(ItemArgs a) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.nX;
-         r += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ix < a.nX;
+         ix += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = a.order[a.begin + ix];
         const uint32_t nc = a.ncand[r];
         const int R = a.R;
         int64_t n = 0;
-        int64_t out = EMIT ? a.item_off[r] : 0;
+        int64_t out = EMIT ? a.item_off[ix] : 0;
         const uint32_t W = (a.dprime[r] + 31) / 32;
         auto emit = [&](uint32_t i0, uint32_t i1, uint32_t u0, uint32_t u1, unsigned long long c) {
             if (EMIT) {
@@ -1090,7 +1112,7 @@ __global__ void k_items(ItemArgs a) {
                 if (rows > rb) emit(rb, rows, 0, 0, acc);
             }
         }
-        if (!EMIT) a.item_cnt[r] = n;
+        if (!EMIT) a.item_cnt[ix] = n;
     }
     if (!EMIT && blockIdx.x == 0 && threadIdx.x == 0) a.item_cnt[a.nX] = 0;
 }
@@ -1127,13 +1149,27 @@ struct Acc {
     unsigned long long tested = 0, leaves = 0, words = 0;
 };
 
-// binom(x, l) for x <= BINOM_TBL (shared memory; binom(256, 8) < 2^64)
 constexpr int BINOM_TBL = 256;
 
-// View of an anchor's candidate masks: P(w, c) and D(w, c).
-struct Masks {
+// Dynamic shared memory of the tuple kernel (staged masks) and its binomial
+// table binom(x, l) for x <= BINOM_TBL (binom(256, 8) < 2^64).
+extern __shared__ __align__(16) uint32_t sm_dyn[];
+__shared__ unsigned long long s_bt[BINOM_TBL + 1];
+
+// Views of an anchor's candidate masks: P(w, c) and D(w, c), word-major.
+// MasksS: staged in the dynamic shared array (32-bit offsets, shared loads);
+// MasksG: read from the candidate pool in global memory.
+struct MasksS {
+    uint32_t stride, W, nc;
+    __device__ __forceinline__ uint32_t P(uint32_t w, uint32_t c) const {
+        return sm_dyn[w * stride + c];
+    }
+    __device__ __forceinline__ uint32_t D(uint32_t w, uint32_t c) const {
+        return sm_dyn[(W + w) * stride + c];
+    }
+};
+struct MasksG {
     const uint32_t *base;
-    const unsigned long long *bt;  // binomial table
     uint32_t stride, W, nc;
     __device__ __forceinline__ uint32_t P(uint32_t w, uint32_t c) const {
         return base[(size_t)w * stride + c];
@@ -1145,8 +1181,8 @@ struct Masks {
 
 // Type counts of a tuple and the binomial sum. T: the lane's common
 // neighbourhood mask; idx[0..R-1]: the tuple's candidate indices.
-template <int R, int WN>
-__device__ __forceinline__ void leaf_narrow(const Masks &m, const uint32_t (&T)[WN],
+template <int R, int WN, class MK>
+__device__ __forceinline__ void leaf_narrow(const MK &m, const uint32_t (&T)[WN],
                                             const uint32_t (&idx)[R], int l, Acc &acc,
                                             unsigned *err) {
     acc.leaves++;
@@ -1221,8 +1257,8 @@ __device__ __forceinline__ void leaf_narrow(const Masks &m, const uint32_t (&T)[
 
 // Extend a warp-uniform prefix (mask `pre`, indices idx[0..L-2]) by every
 // candidate m >= start, lanes over m.
-template <int L, int R, int WN>
-__device__ void expand_narrow(const Masks &m, const uint32_t (&pre)[WN], uint32_t (&idx)[R],
+template <int L, int R, int WN, class MK>
+__device__ void expand_narrow(const MK &m, const uint32_t (&pre)[WN], uint32_t (&idx)[R],
                               uint32_t start, int l, Acc &acc, unsigned *err) {
     const int lane = threadIdx.x & 31;
     for (uint32_t mb = start; mb < m.nc; mb += 32) {
@@ -1265,8 +1301,8 @@ __device__ void expand_narrow(const Masks &m, const uint32_t (&pre)[WN], uint32_
 
 // One work unit: row i (first partner) and a chunk of 32 second partners;
 // for R == 1 a chunk of 32 single partners.
-template <int R, int WN>
-__device__ void unit_narrow(const Masks &m, uint32_t i, uint32_t jc, int l, Acc &acc,
+template <int R, int WN, class MK>
+__device__ void unit_narrow(const MK &m, uint32_t i, uint32_t jc, int l, Acc &acc,
                             unsigned *err) {
     const int lane = threadIdx.x & 31;
     if constexpr (R == 1) {
@@ -1331,8 +1367,8 @@ __device__ void unit_narrow(const Masks &m, uint32_t i, uint32_t jc, int l, Acc 
 // word; warp-uniform prefixes live in a per-warp scratch (level L-1 at
 // pre + (L-2) * wmax).
 
-template <int R>
-__device__ __forceinline__ void leaf_wide(const Masks &m, const uint32_t *pre, uint32_t c,
+template <int R, class MK>
+__device__ __forceinline__ void leaf_wide(const MK &m, const uint32_t *pre, uint32_t c,
                                           const uint32_t (&idx)[R], int l, Acc &acc,
                                           unsigned *err) {
     acc.leaves++;
@@ -1377,8 +1413,8 @@ __device__ __forceinline__ void leaf_wide(const Masks &m, const uint32_t *pre, u
     }
 }
 
-template <int L, int R>
-__device__ void expand_wide(const Masks &m, uint32_t *scratch, uint32_t wmax,
+template <int L, int R, class MK>
+__device__ void expand_wide(const MK &m, uint32_t *scratch, uint32_t wmax,
                             uint32_t (&idx)[R], uint32_t start, int l, Acc &acc, unsigned *err) {
     const int lane = threadIdx.x & 31;
     const uint32_t *pre = scratch + (size_t)(L - 2) * wmax;  // prefix of L-1 partners
@@ -1417,8 +1453,8 @@ __device__ void expand_wide(const Masks &m, uint32_t *scratch, uint32_t wmax,
     }
 }
 
-template <int R>
-__device__ void unit_wide(const Masks &m, uint32_t *scratch, uint32_t wmax, uint32_t i,
+template <int R, class MK>
+__device__ void unit_wide(const MK &m, uint32_t *scratch, uint32_t wmax, uint32_t i,
                           uint32_t jc, int l, Acc &acc, unsigned *err) {
     const int lane = threadIdx.x & 31;
     if constexpr (R == 1) {
@@ -1480,8 +1516,8 @@ __device__ void unit_wide(const Masks &m, uint32_t *scratch, uint32_t wmax, uint
 // below l bits are dropped, which drops only zero binomials.
 
 // Split one part y (already ANDed with P_m) by D_m and add the binomials.
-template <int WN>
-__device__ __forceinline__ void close_part(const Masks &m, const uint32_t (&y)[WN], uint32_t c,
+template <int WN, class MK>
+__device__ __forceinline__ void close_part(const MK &m, const uint32_t (&y)[WN], uint32_t c,
                                            int l, Acc &acc, unsigned *err) {
     uint32_t n = 0;
 #pragma unroll
@@ -1495,15 +1531,41 @@ __device__ __forceinline__ void close_part(const Masks &m, const uint32_t (&y)[W
     acc.words += m.W;
     acc.leaves++;
     if (n <= (uint32_t)BINOM_TBL) {
-        acc.sum.add(m.bt[x1] + m.bt[n - x1]);
+        acc.sum.add(s_bt[x1] + s_bt[n - x1]);
     } else {
         binom_add(acc.sum, x1, l, err);
         binom_add(acc.sum, n - x1, l, err);
     }
 }
 
+// Close part B against candidate c given S = P_c & ~D_c and T = P_c & D_c:
+// the two children B & S and B & T add binom(., l) each (zero below l).
+// Returns whether the part had at least l common neighbours with c.
 template <int WN>
-__device__ void parts_r1(const Masks &m, uint32_t jc, int l, Acc &acc, unsigned *err) {
+__device__ __forceinline__ bool close_st(const uint32_t (&B)[WN], const uint32_t (&S)[WN],
+                                         const uint32_t (&T)[WN], int l, Acc &acc,
+                                         unsigned *err) {
+    uint32_t n0 = 0, n1 = 0;
+#pragma unroll
+    for (int w = 0; w < WN; w++) {
+        n0 += __popc(B[w] & S[w]);
+        n1 += __popc(B[w] & T[w]);
+    }
+    const uint32_t n = n0 + n1;
+    const bool ok = (int)n >= l;
+    if (__any_sync(FULL, ok) && ok) {
+        if (n <= (uint32_t)BINOM_TBL) {
+            acc.sum.add(s_bt[n0] + s_bt[n1]);
+        } else {
+            binom_add(acc.sum, n0, l, err);
+            binom_add(acc.sum, n1, l, err);
+        }
+    }
+    return ok;
+}
+
+template <int WN, class MK>
+__device__ void parts_r1(const MK &m, uint32_t jc, int l, Acc &acc, unsigned *err) {
     const uint32_t c = jc * 32 + (threadIdx.x & 31);
     if (c >= m.nc) return;
     acc.tested++;
@@ -1514,8 +1576,8 @@ __device__ void parts_r1(const Masks &m, uint32_t jc, int l, Acc &acc, unsigned 
 }
 
 // Type parts of candidate i: A0 = P_i & ~D_i (same sign), A1 = P_i & D_i.
-template <int WN>
-__device__ __forceinline__ uint32_t parts_of(const Masks &m, uint32_t i, uint32_t (&A0)[WN],
+template <int WN, class MK>
+__device__ __forceinline__ uint32_t parts_of(const MK &m, uint32_t i, uint32_t (&A0)[WN],
                                              uint32_t (&A1)[WN], int l) {
     uint32_t n0 = 0, n1 = 0;
 #pragma unroll
@@ -1530,34 +1592,40 @@ __device__ __forceinline__ uint32_t parts_of(const Masks &m, uint32_t i, uint32_
     return ((int)n0 >= l ? 1u : 0u) | ((int)n1 >= l ? 2u : 0u);
 }
 
-template <int WN>
-__device__ void parts_r2(const Masks &m, uint32_t i, uint32_t jc, int l, Acc &acc,
+template <int WN, class MK>
+__device__ void parts_r2(const MK &m, uint32_t i, uint32_t jc, int l, Acc &acc,
                          unsigned *err) {
     uint32_t A0[WN], A1[WN];
     const uint32_t va = parts_of<WN>(m, i, A0, A1, l);
     if (!va) return;
     const uint32_t j = i + 1 + jc * 32 + (threadIdx.x & 31);
-    if (j >= m.nc) return;
-    acc.tested++;
-    uint32_t pj[WN];
+    const bool jv = j < m.nc;
+    uint32_t S[WN], T[WN];
 #pragma unroll
-    for (int w = 0; w < WN; w++) pj[w] = w < (int)m.W ? m.P(w, j) : 0u;
+    for (int w = 0; w < WN; w++) {
+        const bool in = jv && w < (int)m.W;
+        const uint32_t p = in ? m.P(w, j) : 0u, d = in ? m.D(w, j) : 0u;
+        S[w] = p & ~d;
+        T[w] = p & d;
+    }
+    uint32_t closes = 0, viable = 0;
     if (va & 1u) {
-        uint32_t y[WN];
-#pragma unroll
-        for (int w = 0; w < WN; w++) y[w] = A0[w] & pj[w];
-        close_part<WN>(m, y, j, l, acc, err);
+        closes++;
+        viable += close_st<WN>(A0, S, T, l, acc, err);
     }
     if (va & 2u) {
-        uint32_t y[WN];
-#pragma unroll
-        for (int w = 0; w < WN; w++) y[w] = A1[w] & pj[w];
-        close_part<WN>(m, y, j, l, acc, err);
+        closes++;
+        viable += close_st<WN>(A1, S, T, l, acc, err);
+    }
+    if (jv) {
+        acc.tested++;
+        acc.leaves += viable;
+        acc.words += (unsigned long long)(closes + viable) * m.W;
     }
 }
 
-template <int WN>
-__device__ void parts_r3(const Masks &m, uint32_t i, uint32_t jc, int l, Acc &acc,
+template <int WN, class MK>
+__device__ void parts_r3(const MK &m, uint32_t i, uint32_t jc, int l, Acc &acc,
                          unsigned *err) {
     const int lane = threadIdx.x & 31;
     uint32_t A0[WN], A1[WN];
@@ -1599,129 +1667,209 @@ __device__ void parts_r3(const Masks &m, uint32_t i, uint32_t jc, int l, Acc &ac
             B[2][w] = A1[w] & p & ~d;
             B[3][w] = A1[w] & p & d;
         }
+        uint32_t tested = 0, closes = 0, viable = 0;
         for (uint32_t mb = js + 1; mb < m.nc; mb += 32) {
             const uint32_t c = mb + lane;
-            if (c >= m.nc) continue;
-            acc.tested++;
-            uint32_t pc[WN];
+            const bool cv = c < m.nc;
+            uint32_t S[WN], T[WN];
 #pragma unroll
-            for (int w = 0; w < WN; w++) pc[w] = w < (int)m.W ? m.P(w, c) : 0u;
+            for (int w = 0; w < WN; w++) {
+                const bool in = cv && w < (int)m.W;
+                const uint32_t p = in ? m.P(w, c) : 0u, d = in ? m.D(w, c) : 0u;
+                S[w] = p & ~d;
+                T[w] = p & d;
+            }
+            tested += cv;
 #pragma unroll
             for (int b = 0; b < 4; b++) {
                 if (!((vbs >> b) & 1u)) continue;
-                uint32_t y[WN];
-#pragma unroll
-                for (int w = 0; w < WN; w++) y[w] = B[b][w] & pc[w];
-                close_part<WN>(m, y, c, l, acc, err);
+                closes += cv;
+                viable += close_st<WN>(B[b], S, T, l, acc, err);
             }
         }
+        acc.tested += tested;
+        acc.leaves += viable;
+        acc.words += (unsigned long long)(closes + viable) * m.W;
     }
 }
 
-// ---- type parts for wide anchors: parts live in the warp's scratch
-// (slot k at scratch + k * wmax), words streamed.
+// ---- type parts for wide anchors (more words than the register paths
+// hold). The words stream through registers: the first partner's parts are
+// recomputed per word from its masks (warp-uniform loads), the lanes' own
+// candidates' S = P & ~D and T = P & D likewise, and all parts are counted in
+// one pass. For three partners the warp-uniform parts of the chosen pair live
+// in a per-warp slot (shared memory up to SLOT_W words, else the warp's
+// global scratch).
 
-__device__ __forceinline__ void wide_close(const Masks &m, const uint32_t *part, uint32_t c,
-                                           int l, Acc &acc, unsigned *err) {
-    uint32_t n = 0, x1 = 0;
-    for (uint32_t w = 0; w < m.W; w++) {
-        uint32_t y = part ? (part[w] & m.P(w, c)) : m.P(w, c);
-        n += __popc(y);
-        x1 += __popc(y & m.D(w, c));
+constexpr int SLOT_W = 32;  // words per part in the shared per-warp slot
+__shared__ uint32_t s_slot[PB_WARPS][4 * SLOT_W];
+
+// Adds binom(x0, l) + binom(x1, l) when x0 + x1 >= l; returns that test.
+__device__ __forceinline__ bool close_x(uint32_t x0, uint32_t x1, int l, Acc &acc, unsigned *err) {
+    const uint32_t n = x0 + x1;
+    const bool ok = (int)n >= l;
+    if (ok) {
+        if (n <= (uint32_t)BINOM_TBL) {
+            acc.sum.add(s_bt[x0] + s_bt[x1]);
+        } else {
+            binom_add(acc.sum, x0, l, err);
+            binom_add(acc.sum, x1, l, err);
+        }
     }
-    acc.words += 2 * m.W;
-    if ((int)n < l) return;
-    acc.leaves++;
-    if (n <= (uint32_t)BINOM_TBL) {
-        acc.sum.add(m.bt[x1] + m.bt[n - x1]);
-    } else {
-        binom_add(acc.sum, x1, l, err);
-        binom_add(acc.sum, n - x1, l, err);
-    }
+    return ok;
 }
 
-// Writes the parts of candidate i to scratch slots 0, 1; returns viability.
-__device__ __forceinline__ uint32_t wide_parts_of(const Masks &m, uint32_t i, uint32_t *scratch,
-                                                  uint32_t wmax, int l) {
+// Viability of candidate i's parts (warp-cooperative): bit 0 same-sign part,
+// bit 1 different-sign part, set when the part holds at least l positions.
+template <class MK>
+__device__ __forceinline__ uint32_t stream_parts_of(const MK &m, uint32_t i, int l) {
     const int lane = threadIdx.x & 31;
     uint32_t n0 = 0, n1 = 0;
-    __syncwarp();
     for (uint32_t w = lane; w < m.W; w += 32) {
-        uint32_t p = m.P(w, i), d = m.D(w, i);
-        scratch[w] = p & ~d;
-        scratch[wmax + w] = p & d;
+        const uint32_t p = m.P(w, i), d = m.D(w, i);
         n0 += __popc(p & ~d);
         n1 += __popc(p & d);
     }
-    __syncwarp();
     n0 = __reduce_add_sync(FULL, n0);
     n1 = __reduce_add_sync(FULL, n1);
     return ((int)n0 >= l ? 1u : 0u) | ((int)n1 >= l ? 2u : 0u);
 }
 
-__device__ void wide_r1(const Masks &m, uint32_t jc, int l, Acc &acc, unsigned *err) {
+template <class MK>
+__device__ void wide_r1(const MK &m, uint32_t jc, int l, Acc &acc, unsigned *err) {
     const uint32_t c = jc * 32 + (threadIdx.x & 31);
     if (c >= m.nc) return;
+    uint32_t x0 = 0, x1 = 0;
+    for (uint32_t w = 0; w < m.W; w++) {
+        const uint32_t p = m.P(w, c), d = m.D(w, c);
+        x0 += __popc(p & ~d);
+        x1 += __popc(p & d);
+    }
+    const bool ok = close_x(x0, x1, l, acc, err);
     acc.tested++;
-    wide_close(m, nullptr, c, l, acc, err);
+    acc.leaves += ok;
+    acc.words += (ok ? 2ull : 1ull) * m.W;
 }
 
-__device__ void wide_r2(const Masks &m, uint32_t *scratch, uint32_t wmax, uint32_t i, uint32_t jc,
-                        int l, Acc &acc, unsigned *err) {
-    const uint32_t va = wide_parts_of(m, i, scratch, wmax, l);
+// Two partners (i, j): the four type counts of every pair in one pass.
+template <class MK>
+__device__ void wide_r2(const MK &m, uint32_t i, uint32_t jc, int l, Acc &acc, unsigned *err) {
+    const uint32_t va = stream_parts_of(m, i, l);
     if (!va) return;
     const uint32_t j = i + 1 + jc * 32 + (threadIdx.x & 31);
     if (j >= m.nc) return;
+    uint32_t x00 = 0, x01 = 0, x10 = 0, x11 = 0;
+#pragma unroll 2
+    for (uint32_t w = 0; w < m.W; w++) {
+        const uint32_t pi = m.P(w, i), di = m.D(w, i);
+        const uint32_t pj = m.P(w, j), dj = m.D(w, j);
+        const uint32_t a0 = pi & ~di, a1 = pi & di, sj = pj & ~dj, tj = pj & dj;
+        x00 += __popc(a0 & sj);
+        x01 += __popc(a0 & tj);
+        x10 += __popc(a1 & sj);
+        x11 += __popc(a1 & tj);
+    }
+    uint32_t closes = 0, viable = 0;
+    if (va & 1u) {
+        closes++;
+        viable += close_x(x00, x01, l, acc, err);
+    }
+    if (va & 2u) {
+        closes++;
+        viable += close_x(x10, x11, l, acc, err);
+    }
     acc.tested++;
-    if (va & 1u) wide_close(m, scratch, j, l, acc, err);
-    if (va & 2u) wide_close(m, scratch + wmax, j, l, acc, err);
+    acc.leaves += viable;
+    acc.words += (unsigned long long)(closes + viable) * m.W;
 }
 
-__device__ void wide_r3(const Masks &m, uint32_t *scratch, uint32_t wmax, uint32_t i, uint32_t jc,
+// Third partners c > js of a pair whose NB viable parts sit in `slot`
+// (NB parts of W words, part k at slot[k * stride ...]).
+template <int NB, bool SHARED, class MK>
+__device__ __forceinline__ void stream_third(const MK &m, const uint32_t *slot, uint32_t stride,
+                                             uint32_t js, int l, Acc &acc, unsigned *err) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t tested = 0, viable = 0;
+    for (uint32_t mb = js + 1; mb < m.nc; mb += 32) {
+        const uint32_t c = mb + lane;
+        if (c >= m.nc) break;
+        uint32_t x0[NB], x1[NB];
+#pragma unroll
+        for (int k = 0; k < NB; k++) x0[k] = x1[k] = 0;
+        for (uint32_t w = 0; w < m.W; w++) {
+            const uint32_t p = m.P(w, c), d = m.D(w, c);
+            const uint32_t sc = p & ~d, tc = p & d;
+#pragma unroll
+            for (int k = 0; k < NB; k++) {
+                const uint32_t bw = SHARED ? s_slot[warp][k * stride + w] : slot[k * stride + w];
+                x0[k] += __popc(bw & sc);
+                x1[k] += __popc(bw & tc);
+            }
+        }
+        tested++;
+#pragma unroll
+        for (int k = 0; k < NB; k++) viable += close_x(x0[k], x1[k], l, acc, err);
+    }
+    acc.tested += tested;
+    acc.leaves += viable;
+    acc.words += (unsigned long long)(NB * tested + viable) * m.W;
+}
+
+// Three partners (i, j, c) for wide anchors. SHARED: the pair's parts fit the
+// shared per-warp slot (W <= SLOT_W); otherwise they go to the warp scratch.
+template <bool SHARED, class MK>
+__device__ void wide_r3(const MK &m, uint32_t *scratch, uint32_t wmax, uint32_t i, uint32_t jc,
                         int l, Acc &acc, unsigned *err) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t va = wide_parts_of(m, i, scratch, wmax, l);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t va = stream_parts_of(m, i, l);
     if (!va) return;
     const uint32_t j = i + 1 + jc * 32 + lane;
-    const bool valid = j + 1 < m.nc;
+    const bool valid = j + 1 < m.nc;  // room for a third partner
     uint32_t vb = 0;
     if (valid) {
-        acc.tested++;
         uint32_t n[4] = {0, 0, 0, 0};
         for (uint32_t w = 0; w < m.W; w++) {
-            uint32_t p = m.P(w, j), d = m.D(w, j);
-            uint32_t a0 = scratch[w], a1 = scratch[wmax + w];
-            n[0] += __popc(a0 & p & ~d);
-            n[1] += __popc(a0 & p & d);
-            n[2] += __popc(a1 & p & ~d);
-            n[3] += __popc(a1 & p & d);
+            const uint32_t pi = m.P(w, i), di = m.D(w, i);
+            const uint32_t pj = m.P(w, j), dj = m.D(w, j);
+            const uint32_t a0 = pi & ~di, a1 = pi & di, sj = pj & ~dj, tj = pj & dj;
+            n[0] += __popc(a0 & sj);
+            n[1] += __popc(a0 & tj);
+            n[2] += __popc(a1 & sj);
+            n[3] += __popc(a1 & tj);
         }
-        acc.words += 4 * m.W;
+        acc.tested++;
+        acc.words += 4ull * m.W;
+#pragma unroll
         for (int b = 0; b < 4; b++) vb |= ((int)n[b] >= l ? 1u : 0u) << b;
         vb &= ((va & 1u) ? 3u : 0u) | ((va & 2u) ? 12u : 0u);
     }
+    uint32_t *slot = SHARED ? s_slot[warp] : scratch;
+    const uint32_t stride = SHARED ? (uint32_t)SLOT_W : wmax;
     uint32_t bal = __ballot_sync(FULL, vb != 0);
     while (bal) {
-        const int s = __ffs(bal) - 1;
+        const int sl = __ffs(bal) - 1;
         bal &= bal - 1;
-        const uint32_t js = i + 1 + jc * 32 + s;
-        const uint32_t vbs = __shfl_sync(FULL, vb, s);
+        const uint32_t js = i + 1 + jc * 32 + sl;
+        const uint32_t vbs = __shfl_sync(FULL, vb, sl);
+        const int nb = __popc(vbs);
+        // the viable parts of (i, js), compacted into slots 0 .. nb-1
         __syncwarp();
         for (uint32_t w = lane; w < m.W; w += 32) {
-            uint32_t p = m.P(w, js), d = m.D(w, js);
-            uint32_t a0 = scratch[w], a1 = scratch[wmax + w];
-            scratch[(2 + 0) * (size_t)wmax + w] = a0 & p & ~d;
-            scratch[(2 + 1) * (size_t)wmax + w] = a0 & p & d;
-            scratch[(2 + 2) * (size_t)wmax + w] = a1 & p & ~d;
-            scratch[(2 + 3) * (size_t)wmax + w] = a1 & p & d;
+            const uint32_t pi = m.P(w, i), di = m.D(w, i);
+            const uint32_t pj = m.P(w, js), dj = m.D(w, js);
+            const uint32_t a0 = pi & ~di, a1 = pi & di, sj = pj & ~dj, tj = pj & dj;
+            const uint32_t part[4] = {a0 & sj, a0 & tj, a1 & sj, a1 & tj};
+            int k = 0;
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+                if ((vbs >> b) & 1u) slot[(k++) * stride + w] = part[b];
         }
         __syncwarp();
-        for (uint32_t mb = js + 1; mb < m.nc; mb += 32) {
-            const uint32_t c = mb + lane;
-            if (c >= m.nc) continue;
-            acc.tested++;
-            for (int b = 0; b < 4; b++)
-                if ((vbs >> b) & 1u) wide_close(m, scratch + (2 + b) * (size_t)wmax, c, l, acc, err);
+        switch (nb) {
+            case 1: stream_third<1, SHARED>(m, slot, stride, js, l, acc, err); break;
+            case 2: stream_third<2, SHARED>(m, slot, stride, js, l, acc, err); break;
+            case 3: stream_third<3, SHARED>(m, slot, stride, js, l, acc, err); break;
+            default: stream_third<4, SHARED>(m, slot, stride, js, l, acc, err); break;
         }
         __syncwarp();
     }
@@ -1754,7 +1902,7 @@ __device__ __forceinline__ void binom_add_r(U128 &acc, unsigned long long x, uns
 }
 
 template <int R, int WPL, int LEV>
-__device__ void pos_expand(const uint32_t *cm, uint32_t dp, uint32_t wc, const uint32_t (&M0)[WPL],
+__device__ void pos_expand(uint32_t dp, uint32_t wc, const uint32_t (&M0)[WPL],
                            const uint32_t (&M1)[WPL], uint32_t start, int l, Acc &acc,
                            unsigned *err) {
     const int lane = threadIdx.x & 31;
@@ -1767,8 +1915,8 @@ __device__ void pos_expand(const uint32_t *cm, uint32_t dp, uint32_t wc, const u
 #pragma unroll
         for (int k = 0; k < WPL; k++) {
             const uint32_t w = lane + 32 * k;
-            X0[k] = w < wc ? (M0[k] & cm[(size_t)q * wc + w]) : 0u;
-            X1[k] = w < wc ? (M1[k] & cm[(size_t)(dp + q) * wc + w]) : 0u;
+            X0[k] = w < wc ? (M0[k] & sm_dyn[q * wc + w]) : 0u;
+            X1[k] = w < wc ? (M1[k] & sm_dyn[(dp + q) * wc + w]) : 0u;
             n += __popc(X0[k]) + __popc(X1[k]);
         }
         n = __reduce_add_sync(FULL, n);
@@ -1783,7 +1931,7 @@ __device__ void pos_expand(const uint32_t *cm, uint32_t dp, uint32_t wc, const u
                 binom_add_r<R>(acc.sum, n, err);
             }
         } else if constexpr (LEV < 8) {
-            pos_expand<R, WPL, LEV + 1>(cm, dp, wc, X0, X1, q + 1, l, acc, err);
+            pos_expand<R, WPL, LEV + 1>(dp, wc, X0, X1, q + 1, l, acc, err);
         }
     }
 }
@@ -1792,7 +1940,7 @@ __device__ void pos_expand(const uint32_t *cm, uint32_t dp, uint32_t wc, const u
 // words): each group of G lanes holds one copy of the prefix (word lane % G)
 // and the 32/G groups of the warp test 32/G extensions q at once.
 template <int R, int G, int LEV>
-__device__ void pos_expand_g(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t m0, uint32_t m1,
+__device__ void pos_expand_g(uint32_t dp, uint32_t wc, uint32_t m0, uint32_t m1,
                              uint32_t start, int l, Acc &acc, unsigned *err) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, grp = lane / G, wl = lane % G;
@@ -1802,8 +1950,8 @@ __device__ void pos_expand_g(const uint32_t *cm, uint32_t dp, uint32_t wc, uint3
         const bool valid = q <= last;
         uint32_t x0 = 0, x1 = 0;
         if (valid && (uint32_t)wl < wc) {
-            x0 = m0 & cm[(size_t)q * wc + wl];
-            x1 = m1 & cm[(size_t)(dp + q) * wc + wl];
+            x0 = m0 & sm_dyn[q * wc + wl];
+            x1 = m1 & sm_dyn[(dp + q) * wc + wl];
         }
         uint32_t n = __popc(x0) + __popc(x1);
 #pragma unroll
@@ -1826,7 +1974,7 @@ __device__ void pos_expand_g(const uint32_t *cm, uint32_t dp, uint32_t wc, uint3
                 const int gs = sl / G;
                 const uint32_t y0 = __shfl_sync(FULL, x0, gs * G + wl);
                 const uint32_t y1 = __shfl_sync(FULL, x1, gs * G + wl);
-                pos_expand_g<R, G, LEV + 1>(cm, dp, wc, y0, y1, (uint32_t)(qb + gs) + 1, l, acc, err);
+                pos_expand_g<R, G, LEV + 1>(dp, wc, y0, y1, (uint32_t)(qb + gs) + 1, l, acc, err);
             }
         }
     }
@@ -1835,29 +1983,29 @@ __device__ void pos_expand_g(const uint32_t *cm, uint32_t dp, uint32_t wc, uint3
 // A position-side unit: first position q1 and, when l >= 3, second position
 // q2 (q2 == 0 means the unit is the whole row q1, used when l == 2).
 template <int R, int G>
-__device__ void pos_unit_g(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
+__device__ void pos_unit_g(uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
                            int l, Acc &acc, unsigned *err) {
     const int wl = (threadIdx.x & 31) % G;
     uint32_t m0 = 0, m1 = 0;
     if ((uint32_t)wl < wc) {
-        m0 = cm[(size_t)q1 * wc + wl];
-        m1 = cm[(size_t)(dp + q1) * wc + wl];
+        m0 = sm_dyn[q1 * wc + wl];
+        m1 = sm_dyn[(dp + q1) * wc + wl];
         if (q2) {
-            m0 &= cm[(size_t)q2 * wc + wl];
-            m1 &= cm[(size_t)(dp + q2) * wc + wl];
+            m0 &= sm_dyn[q2 * wc + wl];
+            m1 &= sm_dyn[(dp + q2) * wc + wl];
         }
     }
     uint32_t n = __popc(m0) + __popc(m1);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) n += __shfl_xor_sync(FULL, n, o);
     if (n < (uint32_t)R) return;
-    if (q2) pos_expand_g<R, G, 3>(cm, dp, wc, m0, m1, q2 + 1, l, acc, err);
-    else pos_expand_g<R, G, 2>(cm, dp, wc, m0, m1, q1 + 1, l, acc, err);
+    if (q2) pos_expand_g<R, G, 3>(dp, wc, m0, m1, q2 + 1, l, acc, err);
+    else pos_expand_g<R, G, 2>(dp, wc, m0, m1, q1 + 1, l, acc, err);
 }
 
 // Wide position-side masks (wc > 32): WPL words per lane, whole warp per node.
 template <int R, int WPL>
-__device__ void pos_unit_w(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
+__device__ void pos_unit_w(uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
                            int l, Acc &acc, unsigned *err) {
     const int lane = threadIdx.x & 31;
     uint32_t M0[WPL], M1[WPL];
@@ -1865,68 +2013,121 @@ __device__ void pos_unit_w(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_
 #pragma unroll
     for (int k = 0; k < WPL; k++) {
         const uint32_t w = lane + 32 * k;
-        M0[k] = w < wc ? cm[(size_t)q1 * wc + w] : 0u;
-        M1[k] = w < wc ? cm[(size_t)(dp + q1) * wc + w] : 0u;
+        M0[k] = w < wc ? sm_dyn[q1 * wc + w] : 0u;
+        M1[k] = w < wc ? sm_dyn[(dp + q1) * wc + w] : 0u;
         if (q2 && w < wc) {
-            M0[k] &= cm[(size_t)q2 * wc + w];
-            M1[k] &= cm[(size_t)(dp + q2) * wc + w];
+            M0[k] &= sm_dyn[q2 * wc + w];
+            M1[k] &= sm_dyn[(dp + q2) * wc + w];
         }
         n += __popc(M0[k]) + __popc(M1[k]);
     }
     n = __reduce_add_sync(FULL, n);
     if (n < (uint32_t)R) return;
-    if (q2) pos_expand<R, WPL, 3>(cm, dp, wc, M0, M1, q2 + 1, l, acc, err);
-    else pos_expand<R, WPL, 2>(cm, dp, wc, M0, M1, q1 + 1, l, acc, err);
+    if (q2) pos_expand<R, WPL, 3>(dp, wc, M0, M1, q2 + 1, l, acc, err);
+    else pos_expand<R, WPL, 2>(dp, wc, M0, M1, q1 + 1, l, acc, err);
 }
 
 template <int R>
-__device__ void pos_unit(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
+__device__ void pos_unit(uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
                          int l, Acc &acc, unsigned *err) {
-    if (wc <= 1) pos_unit_g<R, 1>(cm, dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 2) pos_unit_g<R, 2>(cm, dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 4) pos_unit_g<R, 4>(cm, dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 8) pos_unit_g<R, 8>(cm, dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 16) pos_unit_g<R, 16>(cm, dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 32) pos_unit_g<R, 32>(cm, dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 64) pos_unit_w<R, 2>(cm, dp, wc, q1, q2, l, acc, err);
-    else pos_unit_w<R, 4>(cm, dp, wc, q1, q2, l, acc, err);
+    if (wc <= 1) pos_unit_g<R, 1>(dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 2) pos_unit_g<R, 2>(dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 4) pos_unit_g<R, 4>(dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 8) pos_unit_g<R, 8>(dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 16) pos_unit_g<R, 16>(dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 32) pos_unit_g<R, 32>(dp, wc, q1, q2, l, acc, err);
+    else if (wc <= 64) pos_unit_w<R, 2>(dp, wc, q1, q2, l, acc, err);
+    else pos_unit_w<R, 4>(dp, wc, q1, q2, l, acc, err);
 }
 
-// First position q1 of a position-side item.
-template <int R, int WPL>
-__device__ void pos_row(const uint32_t *cm, uint32_t dp, uint32_t wc, uint32_t q1, int l, Acc &acc,
-                        unsigned *err) {
-    const int lane = threadIdx.x & 31;
-    uint32_t M0[WPL], M1[WPL];
-    uint32_t n = 0;
-#pragma unroll
-    for (int k = 0; k < WPL; k++) {
-        const uint32_t w = lane + 32 * k;
-        M0[k] = w < wc ? cm[(size_t)q1 * wc + w] : 0u;
-        M1[k] = w < wc ? cm[(size_t)(dp + q1) * wc + w] : 0u;
-        n += __popc(M0[k]) + __popc(M1[k]);
+// Candidate-side work units of one item (rows i of first partners, chunks of
+// 32 second partners), taken by the CTA's warps from a shared counter.
+template <int R, class MK>
+__device__ __forceinline__ void cand_units(const MK &m, const Item &it, uint32_t *scratch,
+                                           uint32_t wmax, int l, Acc &acc, unsigned *err,
+                                           uint32_t *s_unit, uint32_t *s_total,
+                                           uint32_t *s_rowpre) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t nc = m.nc;
+    const uint32_t W = m.W;
+    // unit layout
+    const bool split = it.u1 != 0;
+    if (tid == 0) {
+        (*s_unit) = 0;
+        if (split) {
+            (*s_total) = it.u1 - it.u0;
+        } else {
+            uint32_t acc = 0;
+            for (uint32_t i = it.i0; i < it.i1; i++) {
+                s_rowpre[i - it.i0] = acc;
+                acc += (nc - 1 - i + 31) / 32;
+            }
+            s_rowpre[it.i1 - it.i0] = acc;
+            (*s_total) = acc;
+        }
     }
-    n = __reduce_add_sync(FULL, n);
-    if (n < (uint32_t)R) return;
-    pos_expand<R, WPL, 2>(cm, dp, wc, M0, M1, q1 + 1, l, acc, err);
+    __syncthreads();
+    const uint32_t total = (*s_total);
+    for (;;) {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(s_unit, 1u);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= total) break;
+        uint32_t i, jc;
+        if (split) {
+            i = it.i0;
+            jc = it.u0 + u;
+        } else {
+            uint32_t lo = 0, hi = it.i1 - it.i0;  // largest k with rowpre[k] <= u
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (s_rowpre[mid] <= u) lo = mid; else hi = mid;
+            }
+            i = it.i0 + lo;
+            jc = u - s_rowpre[lo];
+        }
+        if constexpr (R == 1) {
+            if (W <= 1) parts_r1<1>(m, jc, l, acc, err);
+            else if (W <= 2) parts_r1<2>(m, jc, l, acc, err);
+            else if (W <= 4) parts_r1<4>(m, jc, l, acc, err);
+            else if (W <= 8) parts_r1<8>(m, jc, l, acc, err);
+            else wide_r1(m, jc, l, acc, err);
+        } else if constexpr (R == 2) {
+            if (W <= 1) parts_r2<1>(m, i, jc, l, acc, err);
+            else if (W <= 2) parts_r2<2>(m, i, jc, l, acc, err);
+            else if (W <= 4) parts_r2<4>(m, i, jc, l, acc, err);
+            else if (W <= 8) parts_r2<8>(m, i, jc, l, acc, err);
+            else wide_r2(m, i, jc, l, acc, err);
+        } else if constexpr (R == 3) {
+            if (W <= 1) parts_r3<1>(m, i, jc, l, acc, err);
+            else if (W <= 2) parts_r3<2>(m, i, jc, l, acc, err);
+            else if (W <= 4) parts_r3<4>(m, i, jc, l, acc, err);
+            else if (W <= (uint32_t)SLOT_W) wide_r3<true>(m, scratch, wmax, i, jc, l, acc, err);
+            else wide_r3<false>(m, scratch, wmax, i, jc, l, acc, err);
+        } else {
+            if (W <= 1) unit_narrow<R, 1>(m, i, jc, l, acc, err);
+            else if (W <= 2) unit_narrow<R, 2>(m, i, jc, l, acc, err);
+            else if (W <= 4) unit_narrow<R, 4>(m, i, jc, l, acc, err);
+            else if (W <= 8) unit_narrow<R, 8>(m, i, jc, l, acc, err);
+            else unit_wide<R>(m, scratch, wmax, i, jc, l, acc, err);
+        }
+    }
 }
 
 template <int R>
 __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
-    extern __shared__ __align__(16) uint32_t sm[];
     __shared__ int s_item;
     __shared__ uint32_t s_unit, s_total;
     __shared__ uint32_t s_rowpre[ROWS_MAX + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned *err = &a.cnt->err;
-    __shared__ unsigned long long s_binom[BINOM_TBL + 1];
     for (int x = tid; x <= BINOM_TBL; x += PB_THREADS) {
         unsigned long long v = 0;
         if (x >= a.l) {
             v = 1;
             for (int i = 1; i <= a.l; i++) v = v * (unsigned long long)(x - a.l + i) / (unsigned long long)i;
         }
-        s_binom[x] = v;
+        s_bt[x] = v;
     }
     __syncthreads();
     uint32_t *scratch =
@@ -1948,7 +2149,7 @@ __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
             // position side: CM0 / CM1 (2 * dp rows of wc words) in shared memory
             const uint32_t dp = a.dprime[r];
             const uint32_t wc = (nc + 31) / 32;
-            for (uint32_t t = tid; t < 2 * dp * wc; t += PB_THREADS) sm[t] = 0;
+            for (uint32_t t = tid; t < 2 * dp * wc; t += PB_THREADS) sm_dyn[t] = 0;
             __syncthreads();
             for (uint32_t c = tid; c < nc; c += PB_THREADS) {
                 const uint32_t cb = 1u << (c & 31), cw = c >> 5;
@@ -1960,7 +2161,7 @@ __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
                         pw &= pw - 1;
                         const uint32_t q = 32 * w + b;
                         const uint32_t part = (dw >> b) & 1u;
-                        atomicOr(&sm[(size_t)(part * dp + q) * wc + cw], cb);
+                        atomicOr(&sm_dyn[(size_t)(part * dp + q) * wc + cw], cb);
                     }
                 }
             }
@@ -1989,88 +2190,29 @@ __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
                 }
                 const uint32_t q1 = it.i0 + lo;
                 const uint32_t q2 = a.l == 2 ? 0u : q1 + 1 + (u - s_rowpre[lo]);
-                pos_unit<R>(sm, dp, wc, q1, q2, a.l, acc, err);
+                pos_unit<R>(dp, wc, q1, q2, a.l, acc, err);
             }
-        } else {
-        Masks m;
-        m.bt = s_binom;
-        m.W = W;
-        m.nc = nc;
-        if (2ull * W * nc <= (unsigned long long)PB_SMEM_WORDS) {
+        } else if (2ull * W * nc <= (unsigned long long)PB_SMEM_WORDS) {
+            // candidate side, masks staged in shared memory
             for (uint32_t t = tid; t < 2 * W * nc; t += PB_THREADS) {
                 uint32_t wd = t / nc, c = t % nc;
-                sm[t] = region[(size_t)wd * rsv + c];
+                sm_dyn[t] = region[(size_t)wd * rsv + c];
             }
-            m.base = sm;
-            m.stride = nc;
+            MasksS ms;
+            ms.W = W;
+            ms.nc = nc;
+            ms.stride = nc;
+            cand_units<R>(ms, it, scratch, a.wmax, a.l, acc, err, &s_unit, &s_total, s_rowpre);
         } else {
-            m.base = region;
-            m.stride = rsv;
+            // candidate side, masks read from the pool
+            MasksG mg;
+            mg.base = region;
+            mg.stride = rsv;
+            mg.W = W;
+            mg.nc = nc;
+            cand_units<R>(mg, it, scratch, a.wmax, a.l, acc, err, &s_unit, &s_total, s_rowpre);
         }
-        // unit layout
-        const bool split = it.u1 != 0;
-        if (tid == 0) {
-            s_unit = 0;
-            if (split) {
-                s_total = it.u1 - it.u0;
-            } else {
-                uint32_t acc = 0;
-                for (uint32_t i = it.i0; i < it.i1; i++) {
-                    s_rowpre[i - it.i0] = acc;
-                    acc += (nc - 1 - i + 31) / 32;
-                }
-                s_rowpre[it.i1 - it.i0] = acc;
-                s_total = acc;
-            }
-        }
-        __syncthreads();
-        const uint32_t total = s_total;
-        for (;;) {
-            uint32_t u = 0;
-            if (lane == 0) u = atomicAdd(&s_unit, 1u);
-            u = __shfl_sync(FULL, u, 0);
-            if (u >= total) break;
-            uint32_t i, jc;
-            if (split) {
-                i = it.i0;
-                jc = it.u0 + u;
-            } else {
-                uint32_t lo = 0, hi = it.i1 - it.i0;  // largest k with rowpre[k] <= u
-                while (hi - lo > 1) {
-                    uint32_t mid = (lo + hi) >> 1;
-                    if (s_rowpre[mid] <= u) lo = mid; else hi = mid;
-                }
-                i = it.i0 + lo;
-                jc = u - s_rowpre[lo];
-            }
-            if constexpr (R == 1) {
-                if (W <= 1) parts_r1<1>(m, jc, a.l, acc, err);
-                else if (W <= 2) parts_r1<2>(m, jc, a.l, acc, err);
-                else if (W <= 4) parts_r1<4>(m, jc, a.l, acc, err);
-                else if (W <= 8) parts_r1<8>(m, jc, a.l, acc, err);
-                else wide_r1(m, jc, a.l, acc, err);
-            } else if constexpr (R == 2) {
-                if (W <= 1) parts_r2<1>(m, i, jc, a.l, acc, err);
-                else if (W <= 2) parts_r2<2>(m, i, jc, a.l, acc, err);
-                else if (W <= 4) parts_r2<4>(m, i, jc, a.l, acc, err);
-                else if (W <= 8) parts_r2<8>(m, i, jc, a.l, acc, err);
-                else wide_r2(m, scratch, a.wmax, i, jc, a.l, acc, err);
-            } else if constexpr (R == 3) {
-                if (W <= 1) parts_r3<1>(m, i, jc, a.l, acc, err);
-                else if (W <= 2) parts_r3<2>(m, i, jc, a.l, acc, err);
-                else if (W <= 4) parts_r3<4>(m, i, jc, a.l, acc, err);
-                else if (W <= 8) parts_r3<8>(m, i, jc, a.l, acc, err);
-                else wide_r3(m, scratch, a.wmax, i, jc, a.l, acc, err);
-            } else {
-                if (W <= 1) unit_narrow<R, 1>(m, i, jc, a.l, acc, err);
-                else if (W <= 2) unit_narrow<R, 2>(m, i, jc, a.l, acc, err);
-                else if (W <= 4) unit_narrow<R, 4>(m, i, jc, a.l, acc, err);
-                else if (W <= 8) unit_narrow<R, 8>(m, i, jc, a.l, acc, err);
-                else unit_wide<R>(m, scratch, a.wmax, i, jc, a.l, acc, err);
-            }
-        }
-        }
-                U128 ws = warp_sum_u128(acc.sum);
+        U128 ws = warp_sum_u128(acc.sum);
         if (lane == 0 && (ws.lo | ws.hi)) {
             atomic_add_u128(a.cnt->total, ws.lo, ws.hi);
             if (a.per_anchor) atomic_add_u128(a.per_anchor + 2 * (size_t)r, ws.lo, ws.hi);
@@ -2107,6 +2249,8 @@ namespace {
 // Relative cost of one position-side prefix node (per candidate word per
 // lane) against one candidate-side tuple word; measured on GB300.
 constexpr unsigned long long kPosNodeCost = 6;
+// Default tuple work items per resident warp of a full launch.
+constexpr unsigned long long kSplitPerWarp = 4;
 
 // Largest x with binom(x, l) computable in 64 bits by the multiplicative
 // formula: every partial product binom(x-l+i, i) * i must stay below 2^64.
@@ -2204,58 +2348,121 @@ struct CountRun {
     int R = 0;
     cudaStream_t s = nullptr;
     DevBuf<Counters> cnt;
-    DevBuf<uint32_t> A_bit, dprime, rsv_c, skey, sval, tk, tv, ncand, npaper, pool, ikey, ival, t1,
-        t2, scratch;
+    DevBuf<uint32_t> A_bit, dprime, rsv_c, skey, sval, tk, tv, ncand, npaper, pool, ikey, ival, t1b,
+        t2b, scratch;
     DevBuf<unsigned long long> e_use, e_all, bucket, per;
-    DevBuf<int64_t> pool_off, dtot, item_off;
+    DevBuf<int64_t> pool_off, dtot, item_off, cum_dev;
     DevBuf<Item> items;
     TwohopArgs ta;
     TupleArgs tu;
     int ga = 0, gs = 0, gt = 0;
     int64_t n_items = 0;
+    unsigned h_items = 0;
     Counters hc;
     CountResult res;
 
     // Launches that execute a planned count (no host synchronisation, no
-    // allocation): usable under stream capture.
-    void launch_count(bool timed, EventTimer *tm) {
+    // allocation): usable under stream capture. Valid when the plan has at
+    // most one anchor group.
+    void launch_count() {
         SBC_CUDA(cudaMemsetAsync(&cnt.ptr->run_begin, 0,
                                  sizeof(Counters) - offsetof(Counters, run_begin), s));
         if (per.ptr) SBC_CUDA(cudaMemsetAsync(per.ptr, 0, per.bytes(), s));
         if (spec.per_graph) SBC_CUDA(cudaMemsetAsync(spec.per_graph, 0, 16 * (size_t)spec.n_graphs, s));
-        if (timed) tm->mark(1, s);
-        if (ga > 0) {
-            if (spec.paper) k_twohop_large<true><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
-            else k_twohop_large<false><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
-            SBC_LAUNCHED();
-            g_launches++;
-        }
-        if (gs > 0) {
-            if (spec.paper) k_twohop_small<true><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
-            else k_twohop_small<false><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
-            SBC_LAUNCHED();
-            g_launches++;
-        }
-        if (timed) tm->mark(2, s);
-        if (timed) tm->mark(3, s);
-        if (gt > 0) {
-            switch (R) {
-                case 1: launch_tuples<1>(gt, s, tu); break;
-                case 2: launch_tuples<2>(gt, s, tu); break;
-                case 3: launch_tuples<3>(gt, s, tu); break;
-                case 4: launch_tuples<4>(gt, s, tu); break;
-                case 5: launch_tuples<5>(gt, s, tu); break;
-                case 6: launch_tuples<6>(gt, s, tu); break;
-                default: launch_tuples<7>(gt, s, tu); break;
-            }
-            g_launches++;
-        }
-        if (timed) tm->mark(4, s);
+        if (groups.empty()) return;
+        launch_twohop((unsigned)groups[0].first, (unsigned)groups[0].second);
+        if (gt > 0) launch_tuple_kernel();
     }
 
-    // Plan (with host reads of sizes) and execute once.
+    // Events around the 2-hop and tuple launches of each group (pairs).
+    std::vector<cudaEvent_t> ev_twohop, ev_tuples;
+    cudaEvent_t new_event(std::vector<cudaEvent_t> &v) {
+        cudaEvent_t e = nullptr;
+        SBC_CUDA(cudaEventCreate(&e));
+        v.push_back(e);
+        return e;
+    }
+    void drop_events() {
+        for (cudaEvent_t e : ev_twohop) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_tuples) cudaEventDestroy(e);
+        ev_twohop.clear();
+        ev_tuples.clear();
+    }
+    static float pairs_ms(const std::vector<cudaEvent_t> &v) {
+        float sum = 0;
+        for (size_t i = 0; i + 1 < v.size(); i += 2) {
+            float t = 0;
+            SBC_CUDA(cudaEventElapsedTime(&t, v[i], v[i + 1]));
+            sum += t;
+        }
+        return sum;
+    }
+    ~CountRun() { drop_events(); }
+
+    // Device words the candidate pool may take at once.
+    int64_t pool_budget_words() const {
+        if (const char *e = getenv("SBC_POOL_BUDGET_KB")) {  // tuning / testing override
+            long long v = atoll(e);
+            if (v > 0) return (int64_t)v * 256;
+        }
+        // the fixed scratch of the no-allocation entry point frees only its
+        // top allocation: one group there
+        if (thread_arena_active()) return INT64_MAX / 8;
+        size_t fr = 0, tot = 0;
+        SBC_CUDA(cudaMemGetInfo(&fr, &tot));
+        return (int64_t)(fr / 4 / 4);
+    }
+
+    void launch_twohop(unsigned a, unsigned b) {
+        ta.large_begin = a;
+        ta.large_end = b < hc.n_big ? b : hc.n_big;
+        ta.small_begin = a > hc.n_big ? a : hc.n_big;
+        ta.small_end = b;
+        if (ga > 0 && ta.large_end > ta.large_begin) {
+            int g = ga;
+            if ((unsigned)g > ta.large_end - ta.large_begin) g = (int)(ta.large_end - ta.large_begin);
+            if (spec.paper) k_twohop_large<true><<<g, PL_THREADS, PL_SMEM, s>>>(ta);
+            else k_twohop_large<false><<<g, PL_THREADS, PL_SMEM, s>>>(ta);
+            SBC_LAUNCHED();
+            g_launches++;
+        }
+        if (gs > 0 && ta.small_end > ta.small_begin) {
+            int g = gs;
+            int64_t need = ((int64_t)ta.small_end - ta.small_begin + PS_WARPS - 1) / PS_WARPS;
+            if ((int64_t)g > need) g = (int)need;
+            if (spec.paper) k_twohop_small<true><<<g, PS_THREADS, PS_SMEM, s>>>(ta);
+            else k_twohop_small<false><<<g, PS_THREADS, PS_SMEM, s>>>(ta);
+            SBC_LAUNCHED();
+            g_launches++;
+        }
+    }
+
+    void launch_tuple_kernel() {
+        switch (R) {
+            case 1: launch_tuples<1>(gt, s, tu); break;
+            case 2: launch_tuples<2>(gt, s, tu); break;
+            case 3: launch_tuples<3>(gt, s, tu); break;
+            case 4: launch_tuples<4>(gt, s, tu); break;
+            case 5: launch_tuples<5>(gt, s, tu); break;
+            case 6: launch_tuples<6>(gt, s, tu); break;
+            default: launch_tuples<7>(gt, s, tu); break;
+        }
+        g_launches++;
+    }
+
+    std::vector<std::pair<int64_t, int64_t>> groups;  // ranges of the sorted anchors
+    float ms_twohop = 0, ms_tuples = 0;
+
+    // Plan (with host reads of sizes) and execute once. Anchors are taken in
+    // heavy-first order in groups whose candidate masks fit the pool budget;
+    // each group runs its 2-hop kernels, item planning and tuple kernel.
     void plan_and_run(EventTimer *tm) {
+        const bool timing = tm != nullptr;
         const int B = 256;
+        groups.clear();
+        drop_events();
+        ta.large_begin = ta.large_end = ta.small_begin = ta.small_end = 0;
+        gt = 0;
         const int l = spec.l;
         R = spec.k - 1;
         cnt.alloc(1, s);
@@ -2277,18 +2484,40 @@ struct CountRun {
                                                   o->B_off.ptr, nX, R, l, spec.shard, spec.nshard,
                                                   spec.paper ? 1 : 0, A_bit.ptr, dprime.ptr,
                                                   e_use.ptr, e_all.ptr, rsv_c.ptr, pool_off.ptr,
-                                                  skey.ptr, sval.ptr, cnt.ptr, SMALL_E);
+                                                  skey.ptr, sval.ptr, cnt.ptr,
+                                                  spec.small_e > 0 ? spec.small_e : SMALL_E);
         SBC_LAUNCHED();
         g_launches++;
-        scan_exclusive_i64(pool_off.ptr, pool_off.ptr, nX + 1, dtot.ptr, s);
         radix_sort_pairs(skey.ptr, sval.ptr, tk.ptr, tv.ptr, nX, 32, s);
         SBC_CUDA(cudaMemsetAsync(ncand.ptr, 0, (size_t)nX * 4, s));
         if (spec.paper) SBC_CUDA(cudaMemsetAsync(npaper.ptr, 0, (size_t)nX * 4, s));
-        int64_t pool_words = 0;
-        SBC_CUDA(cudaMemcpyAsync(&pool_words, dtot.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
         SBC_CUDA(cudaStreamSynchronize(s));
-        pool.alloc((size_t)(pool_words > 0 ? pool_words : 1), s);
+        const int64_t n_act = hc.n_active;
+        // candidate-mask words in heavy-first order, prefix sums, groups
+        std::vector<int64_t> cum(n_act + 1, 0);
+        {
+            DevBuf<int64_t> dcum(n_act + 1, s);
+            k_gather_words<<<grid_for(n_act + 1, B), B, 0, s>>>(sval.ptr, pool_off.ptr, n_act, dcum.ptr);
+            SBC_LAUNCHED();
+            g_launches++;
+            scan_exclusive_i64(dcum.ptr, dcum.ptr, n_act + 1, nullptr, s);
+            SBC_CUDA(cudaMemcpyAsync(cum.data(), dcum.ptr, 8 * (size_t)(n_act + 1),
+                                     cudaMemcpyDeviceToHost, s));
+            SBC_CUDA(cudaStreamSynchronize(s));
+            const int64_t budget = pool_budget_words();
+            int64_t most = 1;
+            for (int64_t a = 0; a < n_act;) {
+                int64_t b = std::upper_bound(cum.begin() + a + 1, cum.end(), cum[a] + budget) -
+                            cum.begin() - 1;
+                if (b <= a) b = a + 1;  // one anchor larger than the budget runs alone
+                groups.emplace_back(a, b);
+                most = std::max(most, cum[b] - cum[a]);
+                a = b;
+            }
+            cum_dev = std::move(dcum);
+            pool.alloc((size_t)most, s);
+        }
         const int sms = sm_count();
 
         ta.A_off = o->A_off.ptr;
@@ -2324,125 +2553,125 @@ struct CountRun {
         if (hc.n_active > hc.n_big) {
             const void *fn = spec.paper ? (const void *)k_twohop_small<true> : (const void *)k_twohop_small<false>;
             gs = sms * blocks_per_sm(fn, PS_THREADS, PS_SMEM);
-            int64_t need = ((int64_t)hc.n_active - hc.n_big + PS_WARPS - 1) / PS_WARPS;
-            if ((int64_t)gs > need) gs = (int)need;
         }
-        // the 2-hop kernels of the first execution
-        if (tm) tm->mark(1, s);
-        if (ga > 0) {
-            if (spec.paper) k_twohop_large<true><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
-            else k_twohop_large<false><<<ga, PL_THREADS, PL_SMEM, s>>>(ta);
-            SBC_LAUNCHED();
-            g_launches++;
-        }
-        if (gs > 0) {
-            if (spec.paper) k_twohop_small<true><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
-            else k_twohop_small<false><<<gs, PS_THREADS, PS_SMEM, s>>>(ta);
-            SBC_LAUNCHED();
-            g_launches++;
-        }
-        if (tm) tm->mark(2, s);
+        const int gb = sms * blocks_per_sm((const void *)k_tuples<1>, PB_THREADS, PB_SMEM);
+        const uint32_t wmax = (uint32_t)((o->max_deg_x + 31) / 32);
+        per.alloc(spec.per_anchor ? 2 * nX : 0, s);
+        if (per.ptr) SBC_CUDA(cudaMemsetAsync(per.ptr, 0, per.bytes(), s));
+        if (spec.per_graph) SBC_CUDA(cudaMemsetAsync(spec.per_graph, 0, 16 * (size_t)spec.n_graphs, s));
+        // warp scratch of the wide paths (more words than the register paths hold)
+        const uint32_t wide_from = R == 3 ? (uint32_t)SLOT_W : R <= 2 ? 0xFFFFFFFFu : 8u;
+        scratch.alloc(wmax > wide_from ? (size_t)gb * PB_WARPS * SCRATCH_SLOTS * wmax : 0, s);
+        tu.ncand = ncand.ptr;
+        tu.dprime = dprime.ptr;
+        tu.rsv_c = rsv_c.ptr;
+        tu.pool_off = pool_off.ptr;
+        tu.pool = pool.ptr;
+        tu.cnt = cnt.ptr;
+        tu.per_anchor = per.ptr;
+        tu.per_graph = spec.per_graph;
+        tu.graph_x0 = spec.graph_x0;
+        tu.n_graphs = spec.n_graphs;
+        tu.wide_scratch = scratch.ptr;
+        tu.wmax = wmax;
+        tu.l = l;
 
-        // tuple phase planning (needs the candidate counts)
         ItemArgs ia;
         ia.ncand = ncand.ptr;
         ia.npaper = spec.paper ? npaper.ptr : nullptr;
         ia.dprime = dprime.ptr;
-        ia.nX = nX;
+        ia.order = sval.ptr;
         ia.R = R;
         ia.l = l;
         ia.method = spec.method;
         ia.pos_unit = spec.pos_unit;
         ia.cnt = cnt.ptr;
-        ia.item_cost = 0;
-        ia.item_off = nullptr;
-        ia.item_cnt = nullptr;
-        ia.items = nullptr;
-        ia.ikey = ia.ival = nullptr;
-        k_anchor_cost<<<grid_for(nX, B), B, 0, s>>>(ia);
-        SBC_LAUNCHED();
-        g_launches++;
-        SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-        SBC_CUDA(cudaStreamSynchronize(s));
-        const int gb = sms * blocks_per_sm((const void *)k_tuples<1>, PB_THREADS, PB_SMEM);
-        unsigned long long ic = hc.cost_total / ((unsigned long long)gb * PB_WARPS * 4ull);
-        if (ic < (1ull << 12)) ic = 1ull << 12;
-        if (ic > (1ull << 30)) ic = 1ull << 30;
-        ia.item_cost = ic;
-        item_off.alloc(nX + 1, s);
-        ia.item_cnt = item_off.ptr;
         n_items = 0;
-        if (hc.cost_total > 0 || R == 1) {
-            k_items<false><<<grid_for(nX, B), B, 0, s>>>(ia);
+        for (const auto &grp : groups) {
+            const int64_t a = grp.first, b = grp.second, na = b - a;
+            // this group's pool offsets and fresh queue heads
+            k_group_offsets<<<grid_for(na, B), B, 0, s>>>(sval.ptr, cum_dev.ptr, a, b, pool_off.ptr);
             SBC_LAUNCHED();
-            scan_exclusive_i64(item_off.ptr, item_off.ptr, nX + 1, dtot.ptr, s);
             g_launches++;
-            SBC_CUDA(cudaMemcpyAsync(&n_items, dtot.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            SBC_CUDA(cudaMemsetAsync(&cnt.ptr->head_large, 0, 3 * sizeof(unsigned), s));
+            SBC_CUDA(cudaMemsetAsync(&cnt.ptr->cost_total, 0, sizeof(unsigned long long), s));
+            cudaEvent_t t0 = timing ? new_event(ev_twohop) : nullptr;
+            cudaEvent_t t1 = timing ? new_event(ev_twohop) : nullptr;
+            if (t0) SBC_CUDA(cudaEventRecord(t0, s));
+            launch_twohop((unsigned)a, (unsigned)b);
+            if (t1) SBC_CUDA(cudaEventRecord(t1, s));
+            // tuple phase planning (needs the candidate counts)
+            ia.begin = a;
+            ia.nX = na;
+            ia.item_cost = 0;
+            ia.item_off = nullptr;
+            ia.item_cnt = nullptr;
+            ia.items = nullptr;
+            ia.ikey = ia.ival = nullptr;
+            k_anchor_cost<<<grid_for(na, B), B, 0, s>>>(ia);
+            SBC_LAUNCHED();
+            g_launches++;
+            SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
             SBC_CUDA(cudaStreamSynchronize(s));
-        }
-        if (n_items > 0xFFFFFFF0ll) fail(SBC_E_UNSUPPORTED, "too many work items");
-        if (tm) tm->mark(3, s);
-        if (n_items > 0) {
-            items.alloc(n_items, s);
-            ikey.alloc(n_items, s);
-            ival.alloc(n_items, s);
-            t1.alloc(n_items, s);
-            t2.alloc(n_items, s);
+            const unsigned long long spw =
+                spec.split_per_warp > 0 ? (unsigned long long)spec.split_per_warp : kSplitPerWarp;
+            unsigned long long ic = hc.cost_total / ((unsigned long long)gb * PB_WARPS * spw);
+            if (ic < (1ull << 12)) ic = 1ull << 12;
+            if (ic > (1ull << 30)) ic = 1ull << 30;
+            ia.item_cost = ic;
+            item_off.alloc(na + 1, s);
+            ia.item_cnt = item_off.ptr;
+            int64_t ng = 0;
+            if (hc.cost_total > 0 || R == 1) {
+                k_items<false><<<grid_for(na, B), B, 0, s>>>(ia);
+                SBC_LAUNCHED();
+                scan_exclusive_i64(item_off.ptr, item_off.ptr, na + 1, dtot.ptr, s);
+                g_launches++;
+                SBC_CUDA(cudaMemcpyAsync(&ng, dtot.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                SBC_CUDA(cudaStreamSynchronize(s));
+            }
+            if (ng > 0xFFFFFFF0ll) fail(SBC_E_UNSUPPORTED, "too many work items");
+            if (ng == 0) continue;
+            items.alloc(ng, s);
+            ikey.alloc(ng, s);
+            ival.alloc(ng, s);
+            t1b.alloc(ng, s);
+            t2b.alloc(ng, s);
             ia.item_off = item_off.ptr;
             ia.items = items.ptr;
             ia.ikey = ikey.ptr;
             ia.ival = ival.ptr;
-            k_items<true><<<grid_for(nX, B), B, 0, s>>>(ia);
+            k_items<true><<<grid_for(na, B), B, 0, s>>>(ia);
             SBC_LAUNCHED();
             g_launches++;
-            radix_sort_pairs(ikey.ptr, ival.ptr, t1.ptr, t2.ptr, n_items, 32, s);
-            unsigned ni = (unsigned)n_items;
-            SBC_CUDA(cudaMemcpyAsync(&cnt.ptr->n_items, &ni, sizeof(unsigned), cudaMemcpyHostToDevice, s));
-            per.alloc(spec.per_anchor ? 2 * nX : 0, s);
-            if (per.ptr) SBC_CUDA(cudaMemsetAsync(per.ptr, 0, per.bytes(), s));
-            if (spec.per_graph) SBC_CUDA(cudaMemsetAsync(spec.per_graph, 0, 16 * (size_t)spec.n_graphs, s));
-            const uint32_t wmax = (uint32_t)((o->max_deg_x + 31) / 32);
-            gt = gb;
-            if ((int64_t)gt > n_items) gt = (int)n_items;
-            scratch.alloc(wmax > 8 ? (size_t)gt * PB_WARPS * SCRATCH_SLOTS * wmax : 0, s);
-            tu.ncand = ncand.ptr;
-            tu.dprime = dprime.ptr;
-            tu.rsv_c = rsv_c.ptr;
-            tu.pool_off = pool_off.ptr;
-            tu.pool = pool.ptr;
+            radix_sort_pairs(ikey.ptr, ival.ptr, t1b.ptr, t2b.ptr, ng, 32, s);
+            h_items = (unsigned)ng;
+            SBC_CUDA(cudaMemcpyAsync(&cnt.ptr->n_items, &h_items, sizeof(unsigned), cudaMemcpyHostToDevice, s));
             tu.items = items.ptr;
             tu.iorder = ival.ptr;
-            tu.cnt = cnt.ptr;
-            tu.per_anchor = per.ptr;
-            tu.per_graph = spec.per_graph;
-            tu.graph_x0 = spec.graph_x0;
-            tu.n_graphs = spec.n_graphs;
-            tu.wide_scratch = scratch.ptr;
-            tu.wmax = wmax;
-            tu.l = l;
-            switch (R) {
-                case 1: launch_tuples<1>(gt, s, tu); break;
-                case 2: launch_tuples<2>(gt, s, tu); break;
-                case 3: launch_tuples<3>(gt, s, tu); break;
-                case 4: launch_tuples<4>(gt, s, tu); break;
-                case 5: launch_tuples<5>(gt, s, tu); break;
-                case 6: launch_tuples<6>(gt, s, tu); break;
-                default: launch_tuples<7>(gt, s, tu); break;
-            }
-            g_launches++;
-        } else if (spec.per_graph) {
-            SBC_CUDA(cudaMemsetAsync(spec.per_graph, 0, 16 * (size_t)spec.n_graphs, s));
+            gt = gb;
+            if ((int64_t)gt > ng) gt = (int)ng;
+            cudaEvent_t t2 = timing ? new_event(ev_tuples) : nullptr;
+            cudaEvent_t t3 = timing ? new_event(ev_tuples) : nullptr;
+            if (t2) SBC_CUDA(cudaEventRecord(t2, s));
+            launch_tuple_kernel();
+            if (t3) SBC_CUDA(cudaEventRecord(t3, s));
+            n_items += ng;
         }
         if (tm) tm->mark(4, s);
         collect();
-        // planning scratch that a replay does not need
+        if (timing) {
+            ms_twohop = pairs_ms(ev_twohop);
+            ms_tuples = pairs_ms(ev_tuples);
+        }
+        // planning scratch a replay does not need
         skey.release();
         tk.release();
         tv.release();
         item_off.release();
         ikey.release();
-        t1.release();
-        t2.release();
+        t1b.release();
+        t2b.release();
     }
 
     // Read the counters after an execution (synchronises the stream).
@@ -2491,10 +2720,23 @@ void countrun_launch(CountRun *r, cudaStream_t s) {
     }
     cudaStream_t keep = r->s;
     r->s = s;
-    r->ta.cnt = r->cnt.ptr;
-    r->launch_count(false, nullptr);
+    if (r->groups.size() > 1) {
+        // a multi-group plan re-plans (host reads between groups)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        SBC_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            r->s = keep;
+            fail(SBC_E_UNSUPPORTED, "a count planned in %zu anchor groups cannot be captured",
+                 r->groups.size());
+        }
+        r->plan_and_run(nullptr);
+    } else {
+        r->launch_count();
+    }
     r->s = keep;
 }
+
+bool countrun_replayable(const CountRun *r) { return r->groups.size() <= 1; }
 
 void countrun_collect(CountRun *r, cudaStream_t s) {
     if (r->nnz == 0 || r->nX == 0) return;
@@ -2505,6 +2747,19 @@ void countrun_collect(CountRun *r, cudaStream_t s) {
 }
 
 void countrun_destroy(CountRun *r) { delete r; }
+
+void apply_tune(CountSpec &spec, const sbc_tune_t *t) {
+    if (!t) return;
+    if (t->small_wedges < 0 || t->small_wedges > SMALL_E)
+        fail(SBC_E_INVAL, "small_wedges must be in [0, %d], got %d", SMALL_E, t->small_wedges);
+    if (t->pos_node_cost < 0 || t->pos_node_cost > (1 << 20))
+        fail(SBC_E_INVAL, "pos_node_cost must be in [0, 2^20], got %d", t->pos_node_cost);
+    if (t->split_per_warp < 0 || t->split_per_warp > 64)
+        fail(SBC_E_INVAL, "split_per_warp must be in [0, 64], got %d", t->split_per_warp);
+    if (t->small_wedges) spec.small_e = t->small_wedges;
+    if (t->pos_node_cost) spec.pos_unit = (unsigned long long)t->pos_node_cost;
+    if (t->split_per_warp) spec.split_per_warp = t->split_per_warp;
+}
 
 unsigned long long pos_node_cost_setting() {
     unsigned long long u = kPosNodeCost;
@@ -2534,6 +2789,7 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     spec.method = (opts && (opts->flags & SBC_COUNT_CANDIDATE_SIDE)) ? 1
                 : (opts && (opts->flags & SBC_COUNT_POSITION_SIDE)) ? 2 : 0;
     spec.pos_unit = pos_node_cost_setting();
+    apply_tune(spec, opts ? opts->tune : nullptr);
     spec.per_anchor = opts && opts->per_anchor;
     if (spec.nshard < 0 || (spec.nshard > 0 && (spec.shard < 0 || spec.shard >= spec.nshard)))
         fail(SBC_E_INVAL, "bad shard %d of %d", spec.shard, spec.nshard);
@@ -2576,10 +2832,10 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
         stats->popc_words = res.popc_words;
         stats->kernels = (int32_t)(g_launches.load() - kernels0);
         if (tm.on) {
-            stats->ms_prepare = tm.ms(0, 1) + tm.ms(2, 3);
-            stats->ms_twohop = tm.ms(1, 2);
-            stats->ms_tuples = tm.ms(3, 4);
             stats->ms_total = tm.ms(0, 4);
+            stats->ms_twohop = run->ms_twohop;
+            stats->ms_tuples = run->ms_tuples;
+            stats->ms_prepare = stats->ms_total - run->ms_twohop - run->ms_tuples;
         }
     }
 }

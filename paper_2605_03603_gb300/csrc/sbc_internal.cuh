@@ -186,6 +186,8 @@ struct CountSpec {
     bool paper = false;     // also count Algorithm 2's candidate sets
     int method = 0;         // 0 cheaper side per anchor, 1 candidate side, 2 position side
     unsigned long long pos_unit = 0;
+    int small_e = 0;         // 2-hop tier threshold in visited wedges (0: default)
+    int split_per_warp = 0;  // tuple work items per warp of a full launch (0: default)
     int shard = 0, nshard = 0;
     bool per_anchor = false;
     unsigned long long *per_graph = nullptr;  // device, 2 words per graph (batches)
@@ -207,8 +209,20 @@ const CountResult &countrun_result(const CountRun *r);
 void countrun_launch(CountRun *r, cudaStream_t s);
 // Reads the counters of the last execution (synchronises s).
 void countrun_collect(CountRun *r, cudaStream_t s);
+// Batches (batch.cu): plan the unions of `gs` and count them once; with
+// capture, record the counting kernels as a CUDA graph for sbc_batch_run.
+sbc_batch *batch_create(const sbc_graph *const *gs, size_t n, int p, int q, bool capture,
+                        const sbc_tune_t *tune, cudaStream_t s);
+const sbc_u128 *batch_first(const sbc_batch *b);
+void batch_destroy(sbc_batch *b);
+
+// False when the plan runs in several anchor groups (no graph capture).
+bool countrun_replayable(const CountRun *r);
 void countrun_destroy(CountRun *r);
 unsigned long long pos_node_cost_setting();
+// Applies launch parameters (NULL or zero fields: defaults) to a count spec;
+// SBC_E_INVAL when a field is out of range.
+void apply_tune(CountSpec &spec, const sbc_tune_t *t);
 
 }  // namespace sbc
 

@@ -32,11 +32,6 @@
 
 namespace sbc {
 
-sbc_batch *batch_create(const sbc_graph *const *gs_in, size_t n, int p, int q, bool capture,
-                        cudaStream_t s);
-const sbc_u128 *batch_first(const sbc_batch *b);
-void batch_destroy(sbc_batch *b);
-
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -131,7 +126,7 @@ void lane_main(sbc_server *s, Lane *lane) {
                 std::vector<const sbc_graph *> gs(gids.size());
                 for (size_t i = 0; i < gids.size(); i++) gs[i] = s->graphs[gids[i]];
                 std::unique_ptr<sbc_batch, void (*)(sbc_batch *)> b(
-                    batch_create(gs.data(), gs.size(), job->p, job->q, false, lane->stream),
+                    batch_create(gs.data(), gs.size(), job->p, job->q, false, nullptr, lane->stream),
                     batch_destroy);
                 const sbc_u128 *first = batch_first(b.get());
                 for (size_t i = 0; i < gids.size(); i++) res[i] = first[i];

@@ -57,3 +57,12 @@ def test_invalid_arguments_rejected_on_host(lib):
     lib.sbc_set_allocator.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     assert lib.sbc_set_allocator(ctypes.c_void_p(1), None, None) == 1
     assert lib.sbc_set_allocator(None, None, None) == 0
+
+
+def test_autotune_rejects_empty_batch_on_host(lib):
+    lib.sbc_autotune.restype = ctypes.c_int
+    lib.sbc_autotune.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    out = (ctypes.c_int32 * 4)()
+    assert lib.sbc_autotune(None, 0, 3, 3, 0, out, None) == 1  # SBC_E_INVAL
+    assert lib.sbc_autotune(None, 0, 3, 3, 0, None, None) == 1

@@ -80,3 +80,53 @@ def test_empty_batches(sbc):
     finally:
         for h in hs:
             h.close()
+
+
+def test_autotuner_choice_counts_exactly(sbc):
+    """The autotuner returns parameters from its search space; a batch planned
+    with them, and single counts with them, stay exact."""
+    gs = mixed_graphs(30, 11) + [sbc_synth.plain_small()]
+    want = [oracle.count(g, 3, 3, side=0) for g in gs]
+    hs = [sbc.graph_from_synth(g) for g in gs]
+    try:
+        t = sbc.sbc_autotune(hs, 3, 3, reps=2)
+        assert t["split_per_warp"] in (0, 1, 2, 4, 8, 16)
+        assert t["small_wedges"] in (0, 64, 128, 256, 512)
+        assert t["pos_node_cost"] in (0, 2, 4, 6, 10, 16, 64, 1 << 20)
+        assert t["ms"] > 0
+        with sbc.Batch(hs, 3, 3, tune=t) as b:
+            assert b.run() == want
+            assert b.run() == want
+        assert [sbc.sbc_count_ex(h, 3, 3, tune=t)[0] for h in hs] == want
+        # a single graph is a batch of one
+        t1 = sbc.sbc_autotune([hs[-1]], 4, 4, reps=1)
+        assert sbc.sbc_count_ex(hs[-1], 4, 4, tune=t1)[0] == oracle.count(gs[-1], 4, 4, side=0)
+    finally:
+        for h in hs:
+            h.close()
+
+
+@pytest.mark.parametrize("tune", [
+    {"small_wedges": 64, "pos_node_cost": 2, "split_per_warp": 16},
+    {"small_wedges": 128, "pos_node_cost": 1 << 20, "split_per_warp": 1},
+    {"small_wedges": 1, "pos_node_cost": 1, "split_per_warp": 64},
+])
+def test_extreme_launch_parameters_exact(sbc, tune):
+    g = sbc_synth.plain_small()
+    with sbc.graph_from_synth(g) as h:
+        for p, q in [(3, 3), (4, 4), (2, 3), (4, 3)]:
+            want = oracle.count(g, p, q, side=0)
+            for side in (0, 1):
+                assert sbc.sbc_count_ex(h, p, q, anchor_side=side, tune=tune)[0] == want
+
+
+def test_launch_parameters_out_of_range_rejected(sbc):
+    g = sbc_synth.plain_small()
+    with sbc.graph_from_synth(g) as h:
+        for bad in [{"small_wedges": 513}, {"split_per_warp": 65}, {"pos_node_cost": -1},
+                    {"small_wedges": -2}]:
+            with pytest.raises(sbc.SbcError) as e:
+                sbc.sbc_count_ex(h, 3, 3, tune=bad)
+            assert e.value.status == 1  # SBC_E_INVAL
+    with pytest.raises(sbc.SbcError):
+        sbc.sbc_autotune([], 3, 3)

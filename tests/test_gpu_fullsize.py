@@ -1,0 +1,89 @@
+"""Parity at the benchmark's full size (200,000 x 100,000, 2,000,000 edges),
+in the launch configuration bench.py times (device-resident input, automatic
+anchor side and method).
+
+The oracle cannot count the whole graph within a test for (4,4), so:
+* per-anchor contributions of a seeded sample of anchors (uniform, nonzero,
+  and the heaviest) are compared with the oracle computed one anchor at a
+  time (anchors whose Algorithm 2 enumeration exceeds a cap are left out and
+  reported);
+* totals are compared through properties that hold at any size: the count is
+  the same whether the anchors are U or V vertices (side swap), and the
+  per-anchor values add up to the total.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import sbc_synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sbc():
+    import torch
+
+    assert torch.cuda.is_available()
+    torch.cuda.init()
+    import paper_2605_03603_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def medium(sbc):
+    import torch
+
+    g = sbc_synth.plain_medium()
+    off = torch.from_numpy(g.offsets).cuda()
+    col = torch.from_numpy(g.cols).cuda()
+    sgn = torch.from_numpy(g.signs).cuda()
+    h = sbc.sbc_graph_create(g.n_u, g.n_v, off, col, sgn)
+    yield g, h
+    h.close()
+
+
+def sample_anchors(per, rng, n_uniform=120, n_nonzero=120, n_top=12):
+    per = np.asarray([float(x) for x in per])
+    nz = np.nonzero(per)[0]
+    top = nz[np.argsort(-per[nz])][:n_top]
+    pick = set(rng.choice(len(per), size=n_uniform, replace=False).tolist())
+    pick |= set(rng.choice(nz, size=min(n_nonzero, len(nz)), replace=False).tolist())
+    pick |= set(top.tolist())
+    return sorted(pick), top
+
+
+@pytest.mark.parametrize("p,q,cap", [(3, 3, 0), (4, 4, 20_000_000)])
+def test_fullsize_sampled_anchors(sbc, medium, p, q, cap):
+    g, h = medium
+    total, st, per = sbc.sbc_count_ex(h, p, q, anchor_side=0, per_anchor=True)
+    assert sum(per) == total
+    rng = np.random.default_rng(100 * p + q)
+    anchors, top = sample_anchors(per, rng)
+    skipped = set()
+    _, want = oracle.count(g, p, q, side=0, per_anchor=True, anchors=anchors,
+                           max_subsets=cap, skipped=skipped)
+    compared = [a for a in anchors if a not in skipped]
+    assert len(compared) >= 200
+    mism = [(a, per[a], want[a]) for a in compared if per[a] != want[a]]
+    assert not mism, mism[:5]
+    # the heaviest compared anchors carry a real share of the count
+    assert sum(per[a] for a in compared) > 0
+
+
+def test_fullsize_totals_side_swap(sbc, medium):
+    g, h = medium
+    for p, q in [(3, 3), (4, 4)]:
+        a, _, _ = sbc.sbc_count_ex(h, p, q, anchor_side=0)
+        b, _, _ = sbc.sbc_count_ex(h, p, q, anchor_side=1)
+        auto = sbc.sbc_count(h, p, q)
+        assert a == b == auto
+
+
+def test_fullsize_33_total_equals_oracle_reference(sbc, medium):
+    """The full (3,3) total against the complete oracle count (all anchors).
+    About a minute of host time on 16 cores."""
+    g, h = medium
+    want = oracle.count(g, 3, 3, side=0)
+    assert sbc.sbc_count(h, 3, 3) == want

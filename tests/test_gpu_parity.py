@@ -292,3 +292,40 @@ def test_small_workload_all_methods(sbc, small, method):
             for side in (0, 1):
                 got, _, _ = sbc.sbc_count_ex(h, p, q, anchor_side=side, method=method)
                 assert got == want, (p, q, side, method)
+
+
+@pytest.mark.parametrize("budget_kb", [1, 64])
+def test_anchor_groups_under_pool_budget(sbc, small, monkeypatch, budget_kb):
+    """A pool budget far below the candidate masks' total splits the anchors
+    into many groups run one after another; counts, per-anchor values and the
+    plan's counters do not change (the tuple-phase counters depend on where
+    work items are split, which follows each group's cost total)."""
+    with sbc.graph_from_synth(small) as h:
+        ref = {pq: sbc.sbc_count_ex(h, *pq, anchor_side=0, per_anchor=True)
+               for pq in [(3, 3), (4, 4), (3, 4)]}
+        monkeypatch.setenv("SBC_POOL_BUDGET_KB", str(budget_kb))
+        for (p, q), (c0, st0, pa0) in ref.items():
+            got, st, pa = sbc.sbc_count_ex(h, p, q, anchor_side=0, per_anchor=True)
+            assert got == c0 == oracle.count(small, p, q, side=0)
+            assert pa == pa0
+            for key in ("candidates", "wedges"):
+                assert st[key] == st0[key], key
+            # more launches than the single-group plan
+            assert st["kernels"] > st0["kernels"]
+
+
+def test_batch_replay_with_anchor_groups(sbc, small, monkeypatch):
+    """A batch whose plan needs several anchor groups is not captured and
+    re-plans on each run; totals stay exact."""
+    gs = [small, sbc_synth.plain_small()]
+    want = [oracle.count(g, 3, 3, side=0) for g in gs]
+    monkeypatch.setenv("SBC_POOL_BUDGET_KB", "4")
+    hs = [sbc.graph_from_synth(g) for g in gs]
+    try:
+        with sbc.Batch(hs, 3, 3) as b:
+            assert b.run() == want
+            assert b.run() == want
+        assert sbc.sbc_count_batch(hs, 3, 3) == want
+    finally:
+        for h in hs:
+            h.close()
