@@ -133,7 +133,7 @@ sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
  *                  relative to one word test of the candidate-side
  *                  enumeration; each anchor takes the cheaper side, so a
  *                  larger value favours the candidate (bitmap AND/POPC over
- *                  candidate tuples) side. 1..2^20, default 6.
+ *                  candidate tuples) side. 1..2^20, default 3.
  *   split_per_warp work items per warp of a full-GPU tuple launch: heavy
  *                  anchors are split into items of about (estimated total
  *                  cost) / (resident warps x split_per_warp). 1..64, default 4.

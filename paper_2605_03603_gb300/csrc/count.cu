@@ -926,7 +926,7 @@ __device__ __forceinline__ unsigned long long unit_cost(uint32_t nc, uint32_t i,
 __device__ __forceinline__ bool pos_fits(uint32_t nc, uint32_t dp, int l) {
     const uint32_t wc = (nc + 31) / 32;
     return dp >= (uint32_t)l && wc <= (uint32_t)POS_MAX_WORDS &&
-           2ull * dp * wc <= (unsigned long long)PB_SMEM_WORDS_PLAN;
+           2ull * dp * (wc | 1u) <= (unsigned long long)PB_SMEM_WORDS_PLAN;
 }
 
 __device__ __forceinline__ unsigned long long pos_row_cost(uint32_t nc, uint32_t dp, uint32_t q1,
@@ -1705,15 +1705,16 @@ constexpr int SLOT_W = 32;  // words per part in the shared per-warp slot
 __shared__ uint32_t s_slot[PB_WARPS][4 * SLOT_W];
 
 // Adds binom(x0, l) + binom(x1, l) when x0 + x1 >= l; returns that test.
-__device__ __forceinline__ bool close_x(uint32_t x0, uint32_t x1, int l, Acc &acc, unsigned *err) {
+__device__ __forceinline__ bool close_x(uint32_t x0, uint32_t x1, int l, U128 &sum,
+                                        unsigned *err) {
     const uint32_t n = x0 + x1;
     const bool ok = (int)n >= l;
     if (ok) {
         if (n <= (uint32_t)BINOM_TBL) {
-            acc.sum.add(s_bt[x0] + s_bt[x1]);
+            sum.add(s_bt[x0] + s_bt[x1]);
         } else {
-            binom_add(acc.sum, x0, l, err);
-            binom_add(acc.sum, x1, l, err);
+            binom_add(sum, x0, l, err);
+            binom_add(sum, x1, l, err);
         }
     }
     return ok;
@@ -1745,7 +1746,7 @@ __device__ void wide_r1(const MK &m, uint32_t jc, int l, Acc &acc, unsigned *err
         x0 += __popc(p & ~d);
         x1 += __popc(p & d);
     }
-    const bool ok = close_x(x0, x1, l, acc, err);
+    const bool ok = close_x(x0, x1, l, acc.sum, err);
     acc.tested++;
     acc.leaves += ok;
     acc.words += (ok ? 2ull : 1ull) * m.W;
@@ -1772,11 +1773,11 @@ __device__ void wide_r2(const MK &m, uint32_t i, uint32_t jc, int l, Acc &acc, u
     uint32_t closes = 0, viable = 0;
     if (va & 1u) {
         closes++;
-        viable += close_x(x00, x01, l, acc, err);
+        viable += close_x(x00, x01, l, acc.sum, err);
     }
     if (va & 2u) {
         closes++;
-        viable += close_x(x10, x11, l, acc, err);
+        viable += close_x(x10, x11, l, acc.sum, err);
     }
     acc.tested++;
     acc.leaves += viable;
@@ -1808,7 +1809,7 @@ __device__ __forceinline__ void stream_third(const MK &m, const uint32_t *slot, 
         }
         tested++;
 #pragma unroll
-        for (int k = 0; k < NB; k++) viable += close_x(x0[k], x1[k], l, acc, err);
+        for (int k = 0; k < NB; k++) viable += close_x(x0[k], x1[k], l, acc.sum, err);
     }
     acc.tested += tested;
     acc.leaves += viable;
@@ -1884,8 +1885,11 @@ __device__ void wide_r3(const MK &m, uint32_t *scratch, uint32_t wmax, uint32_t 
 // where N_Q counts the candidates w with Q inside the same-sign part
 // (P_w & ~D_w) or inside the different-sign part (P_w & D_w) of L[w] (the two
 // parts are disjoint, so w counts at most once). CM0[q] / CM1[q] are the
-// candidates whose same-sign / different-sign part holds position q; a warp
-// walks Q depth first with the candidate words spread over its lanes.
+// candidates whose same-sign / different-sign part holds position q (rows of
+// wc candidate words at an odd stride wcp, so lanes reading different rows hit
+// different banks). A warp walks Q depth first; at every node its lanes scan
+// 32 children q at once, each lane intersecting the node's prefix (held one
+// word per lane and broadcast by shuffles) with row q.
 
 template <int R>
 __device__ __forceinline__ void binom_add_r(U128 &acc, unsigned long long x, unsigned *err) {
@@ -1901,143 +1905,233 @@ __device__ __forceinline__ void binom_add_r(U128 &acc, unsigned long long x, uns
     }
 }
 
+// binom(x, R) for x <= BINOM_TBL, R = the anchor's tuple partners (shared).
+__shared__ unsigned long long s_btR[BINOM_TBL + 1];
+
+// A position-side node's prefix masks, word w of each at lane w % 32, slot
+// w / 32 (passed by value so that it stays in registers across calls).
+template <int WPL>
+struct Pfx {
+    uint32_t m0[WPL], m1[WPL];
+};
+
+// Partial result of a subtree of the position-side walk.
+struct PosOut {
+    U128 sum;
+    uint32_t tested = 0, leaves = 0;
+};
+
+// Children q in [qs, qe] of a node at depth LEV - 1 with prefix M; lanes over
+// q. At depth l a child is a leaf and adds binom(N_Q, R); otherwise children
+// with N >= R are expanded one at a time.
 template <int R, int WPL, int LEV>
-__device__ void pos_expand(uint32_t dp, uint32_t wc, const uint32_t (&M0)[WPL],
-                           const uint32_t (&M1)[WPL], uint32_t start, int l, Acc &acc,
-                           unsigned *err) {
+__device__ __noinline__ PosOut pos_scan(uint32_t dp, uint32_t wc, uint32_t wcp, Pfx<WPL> M,
+                                        uint32_t qs, uint32_t qe, int l, unsigned *err) {
     const int lane = threadIdx.x & 31;
-    // q must leave room for the l - LEV positions still to choose after it
-    const int last = (int)dp - 1 - (l - LEV);
-    for (int qi = (int)start; qi <= last; qi++) {
-        const uint32_t q = (uint32_t)qi;
-        uint32_t X0[WPL], X1[WPL];
+    PosOut out;
+    for (uint32_t qb = qs; qb <= qe; qb += 32) {
+        const uint32_t q = qb + lane;
+        const bool valid = q <= qe;
+        const uint32_t o0 = (valid ? q : qs) * wcp, o1 = (dp + (valid ? q : qs)) * wcp;
         uint32_t n = 0;
 #pragma unroll
         for (int k = 0; k < WPL; k++) {
-            const uint32_t w = lane + 32 * k;
-            X0[k] = w < wc ? (M0[k] & sm_dyn[q * wc + w]) : 0u;
-            X1[k] = w < wc ? (M1[k] & sm_dyn[(dp + q) * wc + w]) : 0u;
-            n += __popc(X0[k]) + __popc(X1[k]);
+            if (32u * k >= wc) break;  // WPL = 4 also serves 65..96 words
+            const uint32_t wend = wc - 32u * k < 32u ? wc - 32u * k : 32u;
+            for (uint32_t sl = 0; sl < wend; sl++) {
+                const uint32_t m0 = __shfl_sync(FULL, M.m0[k], sl), m1 = __shfl_sync(FULL, M.m1[k], sl);
+                const uint32_t w = 32u * k + sl;
+                n += __popc(m0 & sm_dyn[o0 + w]) + __popc(m1 & sm_dyn[o1 + w]);
+            }
         }
-        n = __reduce_add_sync(FULL, n);
-        if (lane == 0) {
-            acc.tested++;
-            acc.words += 2ull * wc;
-        }
-        if (n < (uint32_t)R) continue;
+        out.tested += valid;
         if (LEV == l) {
-            if (lane == 0) {
-                acc.leaves++;
-                binom_add_r<R>(acc.sum, n, err);
+            if (valid && n >= (uint32_t)R) {
+                out.leaves++;
+                if (n <= (uint32_t)BINOM_TBL) out.sum.add(s_btR[n]);
+                else binom_add_r<R>(out.sum, n, err);
             }
         } else if constexpr (LEV < 8) {
-            pos_expand<R, WPL, LEV + 1>(dp, wc, X0, X1, q + 1, l, acc, err);
-        }
-    }
-}
-
-// Lane groups for narrow position-side masks (wc <= G <= 32 candidate
-// words): each group of G lanes holds one copy of the prefix (word lane % G)
-// and the 32/G groups of the warp test 32/G extensions q at once.
-template <int R, int G, int LEV>
-__device__ void pos_expand_g(uint32_t dp, uint32_t wc, uint32_t m0, uint32_t m1,
-                             uint32_t start, int l, Acc &acc, unsigned *err) {
-    constexpr int NG = 32 / G;
-    const int lane = threadIdx.x & 31, grp = lane / G, wl = lane % G;
-    const int last = (int)dp - 1 - (l - LEV);
-    for (int qb = (int)start; qb <= last; qb += NG) {
-        const int q = qb + grp;
-        const bool valid = q <= last;
-        uint32_t x0 = 0, x1 = 0;
-        if (valid && (uint32_t)wl < wc) {
-            x0 = m0 & sm_dyn[q * wc + wl];
-            x1 = m1 & sm_dyn[(dp + q) * wc + wl];
-        }
-        uint32_t n = __popc(x0) + __popc(x1);
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) n += __shfl_xor_sync(FULL, n, o);
-        const bool lead = valid && wl == 0;
-        if (lead) {
-            acc.tested++;
-            acc.words += 2ull * wc;
-        }
-        if (LEV == l) {
-            if (lead && n >= (uint32_t)R) {
-                acc.leaves++;
-                binom_add_r<R>(acc.sum, n, err);
-            }
-        } else if constexpr (LEV < 8) {
-            uint32_t bal = __ballot_sync(FULL, lead && n >= (uint32_t)R);
+            const uint32_t qe2 = dp - 1 - (uint32_t)(l - LEV - 1);  // room for the rest of Q
+            uint32_t bal = __ballot_sync(FULL, valid && n >= (uint32_t)R);
             while (bal) {
                 const int sl = __ffs(bal) - 1;
                 bal &= bal - 1;
-                const int gs = sl / G;
-                const uint32_t y0 = __shfl_sync(FULL, x0, gs * G + wl);
-                const uint32_t y1 = __shfl_sync(FULL, x1, gs * G + wl);
-                pos_expand_g<R, G, LEV + 1>(dp, wc, y0, y1, (uint32_t)(qb + gs) + 1, l, acc, err);
+                const uint32_t qc = qb + sl;
+                if (qc + 1 > qe2) continue;
+                Pfx<WPL> X;
+#pragma unroll
+                for (int k = 0; k < WPL; k++) {
+                    const uint32_t w = lane + 32u * k;
+                    X.m0[k] = w < wc ? (M.m0[k] & sm_dyn[qc * wcp + w]) : 0u;
+                    X.m1[k] = w < wc ? (M.m1[k] & sm_dyn[(dp + qc) * wcp + w]) : 0u;
+                }
+                const PosOut c = pos_scan<R, WPL, LEV + 1>(dp, wc, wcp, X, qc + 1, qe2, l, err);
+                out.sum.add(c.sum);
+                out.tested += c.tested;
+                out.leaves += c.leaves;
             }
         }
     }
+    return out;
 }
 
-// A position-side unit: first position q1 and, when l >= 3, second position
-// q2 (q2 == 0 means the unit is the whole row q1, used when l == 2).
-template <int R, int G>
-__device__ void pos_unit_g(uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
-                           int l, Acc &acc, unsigned *err) {
-    const int wl = (threadIdx.x & 31) % G;
-    uint32_t m0 = 0, m1 = 0;
-    if ((uint32_t)wl < wc) {
-        m0 = sm_dyn[q1 * wc + wl];
-        m1 = sm_dyn[(dp + q1) * wc + wl];
-        if (q2) {
-            m0 &= sm_dyn[q2 * wc + wl];
-            m1 &= sm_dyn[(dp + q2) * wc + wl];
-        }
-    }
-    uint32_t n = __popc(m0) + __popc(m1);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) n += __shfl_xor_sync(FULL, n, o);
-    if (n < (uint32_t)R) return;
-    if (q2) pos_expand_g<R, G, 3>(dp, wc, m0, m1, q2 + 1, l, acc, err);
-    else pos_expand_g<R, G, 2>(dp, wc, m0, m1, q1 + 1, l, acc, err);
-}
-
-// Wide position-side masks (wc > 32): WPL words per lane, whole warp per node.
+// A position-side unit: first position q1 and a chunk of 32 second positions.
 template <int R, int WPL>
-__device__ void pos_unit_w(uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
-                           int l, Acc &acc, unsigned *err) {
+__device__ void pos_unit_scan(uint32_t dp, uint32_t wc, uint32_t wcp, uint32_t q1, uint32_t chunk,
+                              int l, Acc &acc, unsigned *err) {
     const int lane = threadIdx.x & 31;
-    uint32_t M0[WPL], M1[WPL];
+    Pfx<WPL> M;
     uint32_t n = 0;
 #pragma unroll
     for (int k = 0; k < WPL; k++) {
-        const uint32_t w = lane + 32 * k;
-        M0[k] = w < wc ? sm_dyn[q1 * wc + w] : 0u;
-        M1[k] = w < wc ? sm_dyn[(dp + q1) * wc + w] : 0u;
-        if (q2 && w < wc) {
-            M0[k] &= sm_dyn[q2 * wc + w];
-            M1[k] &= sm_dyn[(dp + q2) * wc + w];
-        }
-        n += __popc(M0[k]) + __popc(M1[k]);
+        const uint32_t w = lane + 32u * k;
+        M.m0[k] = w < wc ? sm_dyn[q1 * wcp + w] : 0u;
+        M.m1[k] = w < wc ? sm_dyn[(dp + q1) * wcp + w] : 0u;
+        n += __popc(M.m0[k]) + __popc(M.m1[k]);
     }
     n = __reduce_add_sync(FULL, n);
-    if (n < (uint32_t)R) return;
-    if (q2) pos_expand<R, WPL, 3>(dp, wc, M0, M1, q2 + 1, l, acc, err);
-    else pos_expand<R, WPL, 2>(dp, wc, M0, M1, q1 + 1, l, acc, err);
+    if (n < (uint32_t)R) return;  // no Q through q1 has R candidates
+    const uint32_t qe2 = dp - 1 - (uint32_t)(l - 2);
+    const uint32_t qs = q1 + 1 + 32u * chunk;
+    const uint32_t qe = qs + 31 < qe2 ? qs + 31 : qe2;
+    if (qs > qe) return;
+    const PosOut o = pos_scan<R, WPL, 2>(dp, wc, wcp, M, qs, qe, l, err);
+    acc.sum.add(o.sum);
+    acc.tested += o.tested;
+    acc.leaves += o.leaves;
+    acc.words += 2ull * wc * o.tested;
 }
 
-template <int R>
-__device__ void pos_unit(uint32_t dp, uint32_t wc, uint32_t q1, uint32_t q2,
-                         int l, Acc &acc, unsigned *err) {
-    if (wc <= 1) pos_unit_g<R, 1>(dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 2) pos_unit_g<R, 2>(dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 4) pos_unit_g<R, 4>(dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 8) pos_unit_g<R, 8>(dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 16) pos_unit_g<R, 16>(dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 32) pos_unit_g<R, 32>(dp, wc, q1, q2, l, acc, err);
-    else if (wc <= 64) pos_unit_w<R, 2>(dp, wc, q1, q2, l, acc, err);
-    else pos_unit_w<R, 4>(dp, wc, q1, q2, l, acc, err);
+// Second-position chunks of first position q1 (l-subsets need q2 <= dp + 1 - l).
+__device__ __forceinline__ uint32_t pos_chunks(uint32_t dp, uint32_t q1, int l) {
+    return (dp + 1 - (uint32_t)l - q1 + 31) / 32;
+}
+
+// ---- two partners with the masks in global memory (anchors too large to
+// stage): blocks of BLK_I first partners, whose S / T words a warp keeps in
+// its shared region, against 32 second partners (one per lane) whose words
+// are loaded once per block instead of once per first partner.
+
+constexpr int BLK_I = 8;
+constexpr uint32_t BLK_MAX_W = PB_SMEM_WORDS / PB_WARPS / (2 * BLK_I);  // words per mask
+
+// Tally of one block unit.
+struct BlkOut {
+    U128 sum;
+    uint32_t tested = 0, closes = 0, viable = 0;
+};
+
+__device__ __noinline__ BlkOut block_r2(MasksG m, uint32_t *wsm, uint32_t ib, uint32_t nrows,
+                                        uint32_t jc, int l, unsigned *err) {
+    BlkOut out;
+    const int lane = threadIdx.x & 31;
+    const uint32_t W = m.W;
+    // stage S = P & ~D, T = P & D of rows ib .. ib + nrows - 1; viability bits
+    __syncwarp();
+    for (uint32_t t = lane; t < nrows * W; t += 32) {
+        const uint32_t k = t / W, w = t - k * W;
+        const uint32_t p = m.P(w, ib + k), d = m.D(w, ib + k);
+        wsm[(2 * k) * W + w] = p & ~d;
+        wsm[(2 * k + 1) * W + w] = p & d;
+    }
+    __syncwarp();
+    uint32_t va = 0;  // bit 2k: row k's same-sign part viable, bit 2k+1: different-sign
+    for (uint32_t k = 0; k < nrows; k++) {
+        uint32_t n0 = 0, n1 = 0;
+        for (uint32_t w = lane; w < W; w += 32) {
+            n0 += __popc(wsm[(2 * k) * W + w]);
+            n1 += __popc(wsm[(2 * k + 1) * W + w]);
+        }
+        n0 = __reduce_add_sync(FULL, n0);
+        n1 = __reduce_add_sync(FULL, n1);
+        va |= ((int)n0 >= l ? 1u : 0u) << (2 * k);
+        va |= ((int)n1 >= l ? 1u : 0u) << (2 * k + 1);
+    }
+    if (!va) return out;
+    const uint32_t j = ib + 1 + jc * 32 + lane;
+    if (j >= m.nc) return out;
+    uint32_t x[BLK_I][4];
+#pragma unroll
+    for (int k = 0; k < BLK_I; k++) x[k][0] = x[k][1] = x[k][2] = x[k][3] = 0;
+    for (uint32_t w = 0; w < W; w++) {
+        const uint32_t p = m.P(w, j), d = m.D(w, j);
+        const uint32_t sj = p & ~d, tj = p & d;
+#pragma unroll
+        for (int k = 0; k < BLK_I; k++) {
+            if ((uint32_t)k >= nrows) break;
+            const uint32_t a0 = wsm[(2 * k) * W + w], a1 = wsm[(2 * k + 1) * W + w];
+            x[k][0] += __popc(a0 & sj);
+            x[k][1] += __popc(a0 & tj);
+            x[k][2] += __popc(a1 & sj);
+            x[k][3] += __popc(a1 & tj);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < BLK_I; k++) {
+        if ((uint32_t)k >= nrows || j <= ib + k) break;  // pairs i < j only
+        out.tested++;
+        if ((va >> (2 * k)) & 1u) {
+            out.closes++;
+            out.viable += close_x(x[k][0], x[k][1], l, out.sum, err);
+        }
+        if ((va >> (2 * k + 1)) & 1u) {
+            out.closes++;
+            out.viable += close_x(x[k][2], x[k][3], l, out.sum, err);
+        }
+    }
+    return out;
+}
+
+// Units of a two-partner item with global masks: blocks of BLK_I rows and
+// chunks of 32 second partners after the block's first row.
+__device__ __forceinline__ void block_units(const MasksG &m, const Item &it, int l, Acc &acc,
+                                            unsigned *err, uint32_t *s_unit, uint32_t *s_total,
+                                            uint32_t *s_rowpre) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nc = m.nc;
+    uint32_t *wsm = sm_dyn + (size_t)warp * (2 * BLK_I) * m.W;
+    const bool split = it.u1 != 0;
+    const uint32_t nblk = split ? 1u : (it.i1 - it.i0 + BLK_I - 1) / BLK_I;
+    if (tid == 0) {
+        *s_unit = 0;
+        if (split) {
+            *s_total = it.u1 - it.u0;
+        } else {
+            uint32_t acc_u = 0;
+            for (uint32_t b = 0; b < nblk; b++) {
+                s_rowpre[b] = acc_u;
+                acc_u += (nc - 1 - (it.i0 + b * BLK_I) + 31) / 32;
+            }
+            s_rowpre[nblk] = acc_u;
+            *s_total = acc_u;
+        }
+    }
+    __syncthreads();
+    const uint32_t total = *s_total;
+    for (;;) {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(s_unit, 1u);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= total) break;
+        BlkOut o;
+        if (split) {
+            o = block_r2(m, wsm, it.i0, 1, it.u0 + u, l, err);
+        } else {
+            uint32_t lo = 0, hi = nblk;  // largest b with rowpre[b] <= u
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (s_rowpre[mid] <= u) lo = mid; else hi = mid;
+            }
+            const uint32_t ib = it.i0 + lo * BLK_I;
+            const uint32_t nrows = it.i1 - ib < (uint32_t)BLK_I ? it.i1 - ib : (uint32_t)BLK_I;
+            o = block_r2(m, wsm, ib, nrows, u - s_rowpre[lo], l, err);
+        }
+        acc.sum.add(o.sum);
+        acc.tested += o.tested;
+        acc.leaves += o.viable;
+        acc.words += (unsigned long long)(o.closes + o.viable) * m.W;
+    }
 }
 
 // Candidate-side work units of one item (rows i of first partners, chunks of
@@ -2128,6 +2222,12 @@ __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
             for (int i = 1; i <= a.l; i++) v = v * (unsigned long long)(x - a.l + i) / (unsigned long long)i;
         }
         s_bt[x] = v;
+        unsigned long long vr = 0;
+        if (x >= R) {
+            vr = 1;
+            for (int i = 1; i <= R; i++) vr = vr * (unsigned long long)(x - R + i) / (unsigned long long)i;
+        }
+        s_btR[x] = vr;
     }
     __syncthreads();
     uint32_t *scratch =
@@ -2146,10 +2246,10 @@ __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
         const uint32_t *region = a.pool + a.pool_off[r];
         Acc acc;
         if (it.u1 == POS_ITEM) {
-            // position side: CM0 / CM1 (2 * dp rows of wc words) in shared memory
+            // position side: CM0 / CM1 (2 * dp rows of wc words, stride wcp) in shared memory
             const uint32_t dp = a.dprime[r];
-            const uint32_t wc = (nc + 31) / 32;
-            for (uint32_t t = tid; t < 2 * dp * wc; t += PB_THREADS) sm_dyn[t] = 0;
+            const uint32_t wc = (nc + 31) / 32, wcp = wc | 1u;
+            for (uint32_t t = tid; t < 2 * dp * wcp; t += PB_THREADS) sm_dyn[t] = 0;
             __syncthreads();
             for (uint32_t c = tid; c < nc; c += PB_THREADS) {
                 const uint32_t cb = 1u << (c & 31), cw = c >> 5;
@@ -2161,16 +2261,16 @@ __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
                         pw &= pw - 1;
                         const uint32_t q = 32 * w + b;
                         const uint32_t part = (dw >> b) & 1u;
-                        atomicOr(&sm_dyn[(size_t)(part * dp + q) * wc + cw], cb);
+                        atomicOr(&sm_dyn[(part * dp + q) * wcp + cw], cb);
                     }
                 }
             }
-            // units: rows q1 (l == 2) or pairs (q1, q2) with q2 <= dp - l + 1
+            // units: first position q1 and a chunk of 32 second positions
             if (tid == 0) {
                 uint32_t acc_u = 0;
                 for (uint32_t q = it.i0; q < it.i1; q++) {
                     s_rowpre[q - it.i0] = acc_u;
-                    acc_u += a.l == 2 ? 1u : (dp - a.l + 1 - q);
+                    acc_u += pos_chunks(dp, q, a.l);
                 }
                 s_rowpre[it.i1 - it.i0] = acc_u;
                 s_total = acc_u;
@@ -2189,8 +2289,10 @@ __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
                     if (s_rowpre[mid] <= u) lo = mid; else hi = mid;
                 }
                 const uint32_t q1 = it.i0 + lo;
-                const uint32_t q2 = a.l == 2 ? 0u : q1 + 1 + (u - s_rowpre[lo]);
-                pos_unit<R>(dp, wc, q1, q2, a.l, acc, err);
+                const uint32_t chunk = u - s_rowpre[lo];
+                if (wc <= 32) pos_unit_scan<R, 1>(dp, wc, wcp, q1, chunk, a.l, acc, err);
+                else if (wc <= 64) pos_unit_scan<R, 2>(dp, wc, wcp, q1, chunk, a.l, acc, err);
+                else pos_unit_scan<R, 4>(dp, wc, wcp, q1, chunk, a.l, acc, err);
             }
         } else if (2ull * W * nc <= (unsigned long long)PB_SMEM_WORDS) {
             // candidate side, masks staged in shared memory
@@ -2210,7 +2312,15 @@ __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
             mg.stride = rsv;
             mg.W = W;
             mg.nc = nc;
-            cand_units<R>(mg, it, scratch, a.wmax, a.l, acc, err, &s_unit, &s_total, s_rowpre);
+            bool blocked = false;
+            if constexpr (R == 2) {
+                if (W > 8 && W <= BLK_MAX_W) {
+                    block_units(mg, it, a.l, acc, err, &s_unit, &s_total, s_rowpre);
+                    blocked = true;
+                }
+            }
+            if (!blocked)
+                cand_units<R>(mg, it, scratch, a.wmax, a.l, acc, err, &s_unit, &s_total, s_rowpre);
         }
         U128 ws = warp_sum_u128(acc.sum);
         if (lane == 0 && (ws.lo | ws.hi)) {
@@ -2248,7 +2358,7 @@ namespace {
 
 // Relative cost of one position-side prefix node (per candidate word per
 // lane) against one candidate-side tuple word; measured on GB300.
-constexpr unsigned long long kPosNodeCost = 6;
+constexpr unsigned long long kPosNodeCost = 3;
 // Default tuple work items per resident warp of a full launch.
 constexpr unsigned long long kSplitPerWarp = 4;
 

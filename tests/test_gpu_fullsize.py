@@ -1,15 +1,16 @@
 """Parity at the benchmark's full size (200,000 x 100,000, 2,000,000 edges),
 in the launch configuration bench.py times (device-resident input, automatic
-anchor side and method).
+anchor side and method), and on the 60,000,000-edge workload.
 
 The oracle cannot count the whole graph within a test for (4,4), so:
 * per-anchor contributions of a seeded sample of anchors (uniform, nonzero,
   and the heaviest) are compared with the oracle computed one anchor at a
   time (anchors whose Algorithm 2 enumeration exceeds a cap are left out and
   reported);
-* totals are compared through properties that hold at any size: the count is
-  the same whether the anchors are U or V vertices (side swap), and the
-  per-anchor values add up to the total.
+* totals are compared through properties that hold at any size: the (3,3)
+  count is the same whether the anchors are U or V vertices (side swap), and
+  the per-anchor values add up to the total; the full (3,3) total is also
+  compared with the oracle's.
 """
 import numpy as np
 import pytest
@@ -73,12 +74,15 @@ def test_fullsize_sampled_anchors(sbc, medium, p, q, cap):
 
 
 def test_fullsize_totals_side_swap(sbc, medium):
+    """(3,3) anchored on U and on V agree. The (4,4) swap is left to the small
+    graphs: anchored on V this graph has about 100x the candidate-side work
+    (V-anchors with up to 10^4 candidates and too many for the position side),
+    which the cost model never picks."""
     g, h = medium
-    for p, q in [(3, 3), (4, 4)]:
-        a, _, _ = sbc.sbc_count_ex(h, p, q, anchor_side=0)
-        b, _, _ = sbc.sbc_count_ex(h, p, q, anchor_side=1)
-        auto = sbc.sbc_count(h, p, q)
-        assert a == b == auto
+    a, _, _ = sbc.sbc_count_ex(h, 3, 3, anchor_side=0)
+    b, _, _ = sbc.sbc_count_ex(h, 3, 3, anchor_side=1)
+    auto = sbc.sbc_count(h, 3, 3)
+    assert a == b == auto
 
 
 def test_fullsize_33_total_equals_oracle_reference(sbc, medium):
@@ -87,3 +91,39 @@ def test_fullsize_33_total_equals_oracle_reference(sbc, medium):
     g, h = medium
     want = oracle.count(g, 3, 3, side=0)
     assert sbc.sbc_count(h, 3, 3) == want
+
+
+# ------------------------------------------------------------------ 60M edges
+
+@pytest.fixture(scope="module")
+def large(sbc):
+    """5,000,000 x 1,000,000, 60,000,000 edges, signs packed one bit per
+    edge, int64 row offsets (the largest workload)."""
+    g = sbc_synth.plain_large()
+    h = sbc.graph_from_synth(g, device=True, sign_bits=True)
+    yield g, h
+    h.close()
+
+
+def test_large_33_sampled_anchors(sbc, large):
+    """Per-anchor (3,3) contributions of the 60M-edge graph on its preferred
+    anchor side (V) against the oracle one anchor at a time; anchors whose
+    Algorithm 2 enumeration exceeds the cap are left out. Totals: per-anchor
+    values add up to the count."""
+    g, h = large
+    info = sbc.sbc_graph_info(h)
+    side = 0 if info["wedges_anchor_u"] <= info["wedges_anchor_v"] else 1
+    total, st, per = sbc.sbc_count_ex(h, 3, 3, anchor_side=side, per_anchor=True)
+    assert st["anchor_side"] == side
+    assert sum(per) == total
+    assert total == sbc.sbc_count(h, 3, 3)
+    rng = np.random.default_rng(333)
+    anchors, _ = sample_anchors(per, rng, n_uniform=100, n_nonzero=150, n_top=8)
+    skipped = set()
+    _, want = oracle.count(g, 3, 3, side=side, per_anchor=True, anchors=anchors,
+                           max_subsets=2_000_000, skipped=skipped)
+    compared = [a for a in anchors if a not in skipped]
+    assert len(compared) >= 150
+    mism = [(a, per[a], want[a]) for a in compared if per[a] != want[a]]
+    assert not mism, mism[:5]
+    assert sum(per[a] for a in compared) > 0

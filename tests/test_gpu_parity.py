@@ -329,3 +329,69 @@ def test_batch_replay_with_anchor_groups(sbc, small, monkeypatch):
     finally:
         for h in hs:
             h.close()
+
+
+def dense_faction_graph(m, n, density, seed, flip=0.05):
+    rng = np.random.default_rng(seed)
+    u, v = np.divmod(np.arange(m * n), n)
+    keep = rng.random(m * n) < density
+    lab_u = rng.choice([-1, 1], m)
+    lab_v = rng.choice([-1, 1], n)
+    s = (lab_u[u] * lab_v[v]).astype(np.int8)
+    s[rng.random(m * n) < flip] *= -1
+    return sbc_synth.from_edges(m, n, u[keep], v[keep], s[keep])
+
+
+def sparse_with_block(m, n, rho_block, rho_other, bu, bv, seed, flip=0.05):
+    """Sparse random edges (density rho_block on bu planted U-vertices,
+    rho_other on the rest) plus a complete bu x bv block with faction signs.
+    The planted vertices have the lowest degrees, so they come first in the
+    priority order with every other vertex as a partner; among themselves
+    they share the block, so three-partner tuples survive."""
+    rng = np.random.default_rng(seed)
+    bu_ids = rng.choice(m, bu, replace=False)
+    rho = np.full(m, rho_other)
+    rho[bu_ids] = rho_block
+    mask = rng.random((m, n)) < rho[:, None]
+    mask[np.ix_(bu_ids, rng.choice(n, bv, replace=False))] = True
+    u, v = np.nonzero(mask)
+    lab_u = rng.choice([-1, 1], m)
+    lab_v = rng.choice([-1, 1], n)
+    s = (lab_u[u] * lab_v[v]).astype(np.int8)
+    s[rng.random(len(u)) < flip] *= -1
+    return sbc_synth.from_edges(m, n, u, v, s), bu_ids
+
+
+def lowest_priority(g, k, among=None):
+    """The k U-vertices first in the priority order (degree, then id), or the
+    first k of `among`: they have the most higher-priority partners."""
+    deg = np.diff(g.offsets)
+    order = np.lexsort((np.arange(g.n_u), deg)).tolist()
+    if among is not None:
+        keep = set(int(x) for x in among)
+        order = [x for x in order if x in keep]
+    return order[:k]
+
+
+@pytest.mark.parametrize("case", ["pairs", "pairs_q4", "triples_slot", "triples_scratch"])
+def test_global_mask_paths(sbc, case):
+    """Anchors whose candidate masks exceed the tuple kernel's shared memory
+    (two partners: blocked path; three partners: shared per-warp slot and
+    global scratch), per anchor against the oracle; the whole count against
+    the other anchor side."""
+    if case.startswith("pairs"):
+        g = dense_faction_graph(1200, 700, 0.6, seed=17)
+        anchors = lowest_priority(g, 6)
+        p, q = (3, 3) if case == "pairs" else (3, 4)
+    else:
+        rho_b, rho_o = (0.03, 0.05) if case == "triples_slot" else (0.04, 0.06)
+        g, block = sparse_with_block(420, 25000, rho_b, rho_o, 30, 250, seed=23)
+        anchors = lowest_priority(g, 6, among=block)
+        p, q = 4, 3
+    with sbc.graph_from_synth(g) as h:
+        total, st, per = sbc.sbc_count_ex(h, p, q, anchor_side=0, per_anchor=True)
+        other, _, _ = sbc.sbc_count_ex(h, p, q, anchor_side=1)
+    assert total == other
+    _, want = oracle.count(g, p, q, side=0, per_anchor=True, anchors=anchors)
+    assert [per[a] for a in anchors] == [want[a] for a in anchors]
+    assert sum(want[a] for a in anchors) > 0
