@@ -40,6 +40,10 @@ METRIC = "anchor tuples/sec and seconds to exact balanced (3,3) count; batched g
 WORKLOAD = "plain-200k-100k-2M"
 PQ = [(3, 3), (4, 4)]
 POPC_PER_CLK_PER_SM = 16  # 32-bit population count throughput per SM per clock
+# DRAM bytes (read + write) per tuple-kernel launch, mean of the (3,3) and (4,4)
+# launches, from one ncu capture of the current kernel
+# (profiles/k_tuples_traffic_plain-200k-100k-2M.md); None where not captured.
+TUPLE_TRAFFIC = {"plain-200k-100k-2M": 264_800_128}
 
 
 def _dist():
@@ -401,7 +405,7 @@ def run_ours(args):
     peak = sm_count * POPC_PER_CLK_PER_SM * clk * 1e6 / 1e12
     roof = {"kernel": "k_tuples (tuple enumeration, AND/POPC type counts)", "bound": "alu",
             "achieved": achieved, "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": TUPLE_TRAFFIC.get(WORKLOAD) if PQ == [(3, 3), (4, 4)] else None,
             "peak_basis": f"{sm_count} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {clk:.0f} MHz "
                           f"(median SM clock sampled under load)",
             "share_of_step": float(np.mean(tup_ms) / np.mean(step_ms))}
