@@ -13,13 +13,23 @@ the (4,4) count. The metric is anchor tuples per second: the number of
 binom(|C(u)|, k-1), counted exactly once, outside the timed region), over the
 step time. Between timed steps L2 is flushed by writing a 512 MiB buffer.
 
+The line also carries: the tuple kernel's roofline (population counts per
+second against SMs x 16 per clock x the sampled SM clock, with its DRAM bytes
+per launch from an ncu capture), the 2-hop kernels' bytes per second, an
+end-to-end figure through the public API from pinned host buffers, the oracle
+timed on the host's cores on an anchor sample, a batch leg (graphs/s of the
+per-graph path, one batched count, a CUDA-graph replay and a replay with
+autotuned launch parameters) and a serving leg (p50/p99 and throughput under
+Poisson arrivals against one-at-a-time serving of the same arrivals).
+
 --impl reference runs the CPU oracle (Algorithm 2 in plain C, all host cores)
-on a bounded random sample of anchors of the same workload and reports the
-same metric.
+on a bounded random sample of anchors of the (3,3) count of the same workload
+and reports the same metric.
 
 Multi-GPU (torchrun): anchors are sharded by rank (anchor rank mod N) over a
-replicated graph; each rank counts its shard; partial counts are summed on the
-host. Total work is fixed, so scaling is strong.
+replicated graph; each rank counts its shard; partial counts are summed
+exactly on the host (paper_2605_03603_gb300.dist). Total work is fixed, so
+scaling is strong.
 """
 from __future__ import annotations
 
@@ -209,8 +219,10 @@ def batch_leg(sbc, torch, args):
     with sbc.Batch(hs, p, q) as b:
         b.run()
         replay, t_replay = timed(b.run, 5)
+    # the autotuner times a sample of the batch (at most 1,000 graphs)
+    n_tune = min(len(hs), 1000)
     t0 = time.perf_counter()
-    tune = sbc.sbc_autotune(hs, p, q)
+    tune = sbc.sbc_autotune(hs[:n_tune], p, q)
     t_tune = time.perf_counter() - t0
     with sbc.Batch(hs, p, q, tune=tune) as b:
         b.run()
@@ -222,7 +234,8 @@ def batch_leg(sbc, torch, args):
     return {"graphs": n, "edges": int(edges), "pq": "(3,3)", "generate_s": t_gen,
             "create_s": t_create, "plain_graphs_per_s": n / t_plain,
             "batched_graphs_per_s": n / t_batch, "replay_graphs_per_s": n / t_replay,
-            "tuned_replay_graphs_per_s": n / t_tuned, "autotune_s": t_tune, "tune": tune,
+            "tuned_replay_graphs_per_s": n / t_tuned, "autotune_s": t_tune,
+            "autotune_graphs": n_tune, "tune": tune,
             "batched_vs_plain": t_plain / t_batch, "replay_vs_plain": t_plain / t_replay,
             "tuned_replay_vs_plain": t_plain / t_tuned, "total_count": sum(plain)}
 

@@ -128,7 +128,7 @@ sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
  *   small_wedges   anchors whose 2-hop visit (Algorithm 2's cnt loop) covers
  *                  at most this many wedges take the warp-per-anchor 2-hop
  *                  kernel; the others take a whole CTA of 16 warps each.
- *                  1..512, default 512.
+ *                  1..64, default 64.
  *   pos_node_cost  cost of one prefix node of the position-side enumeration
  *                  relative to one word test of the candidate-side
  *                  enumeration; each anchor takes the cheaper side, so a
@@ -239,7 +239,7 @@ sbc_status sbc_batch_destroy(sbc_batch *b);
  * single graph is a batch of one) for (p, q) under candidate launch
  * parameters and writes the fastest to *out (out->ms = its time per count).
  * The search is coordinate descent from the defaults over split_per_warp
- * {1, 2, 4, 8, 16}, small_wedges {64, 128, 256, 512} and pos_node_cost
+ * {1, 2, 4, 8, 16}, small_wedges {16, 32, 48, 64} and pos_node_cost
  * {2, 4, 6, 10, 16, 64, 2^20}; each candidate is planned once and its
  * counting kernels timed (best of `reps`, 0 = 3) with CUDA events on
  * `stream`. Every candidate must produce the same counts, or the call fails

@@ -346,7 +346,7 @@ void autotune(const sbc_graph *const *gs, size_t n, int p, int q, int reps, sbc_
     sbc_tune_t cur{0, 0, 0, 0.0f};
     cur.ms = measure(cur);
     const int splits[] = {1, 2, 4, 8, 16};
-    const int smalls[] = {64, 128, 256, 512};
+    const int smalls[] = {16, 32, 48, 64};
     const int costs[] = {2, 4, 6, 10, 16, 64, 1 << 20};
     auto sweep = [&](int32_t sbc_tune_t::*field, const int *vals, int nv) {
         sbc_tune_t best = cur;

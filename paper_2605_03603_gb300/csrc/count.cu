@@ -326,6 +326,11 @@ constexpr int PS_THREADS = 256;
 constexpr int PS_WARPS = PS_THREADS / 32;
 constexpr int PS_HS = 1024;            // slots per warp
 constexpr int SMALL_E = PS_HS / 2;     // visited wedges of a small anchor (load <= 1/2)
+// Default and largest tier threshold. Anchors of 256-512 visited wedges on
+// the warp tier lost candidate-mask bits on some graphs of the 10,000-graph
+// batch recipe (the CTA tier counts them exactly); until the cause is found
+// the warp tier takes anchors of at most 64 wedges.
+constexpr int SMALL_E_MAX = 64;
 constexpr size_t PS_SMEM = (size_t)PS_WARPS * PS_HS * 12;
 
 // Visit the anchor's 2-hop entries with one warp. fn(w, sdiff, bit).
@@ -2595,7 +2600,7 @@ struct CountRun {
                                                   spec.paper ? 1 : 0, A_bit.ptr, dprime.ptr,
                                                   e_use.ptr, e_all.ptr, rsv_c.ptr, pool_off.ptr,
                                                   skey.ptr, sval.ptr, cnt.ptr,
-                                                  spec.small_e > 0 ? spec.small_e : SMALL_E);
+                                                  spec.small_e > 0 ? spec.small_e : SMALL_E_MAX);
         SBC_LAUNCHED();
         g_launches++;
         radix_sort_pairs(skey.ptr, sval.ptr, tk.ptr, tv.ptr, nX, 32, s);
@@ -2860,8 +2865,8 @@ void countrun_destroy(CountRun *r) { delete r; }
 
 void apply_tune(CountSpec &spec, const sbc_tune_t *t) {
     if (!t) return;
-    if (t->small_wedges < 0 || t->small_wedges > SMALL_E)
-        fail(SBC_E_INVAL, "small_wedges must be in [0, %d], got %d", SMALL_E, t->small_wedges);
+    if (t->small_wedges < 0 || t->small_wedges > SMALL_E_MAX)
+        fail(SBC_E_INVAL, "small_wedges must be in [0, %d], got %d", SMALL_E_MAX, t->small_wedges);
     if (t->pos_node_cost < 0 || t->pos_node_cost > (1 << 20))
         fail(SBC_E_INVAL, "pos_node_cost must be in [0, 2^20], got %d", t->pos_node_cost);
     if (t->split_per_warp < 0 || t->split_per_warp > 64)

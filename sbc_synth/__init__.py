@@ -31,6 +31,7 @@ import dataclasses
 import math
 import os
 import subprocess
+import threading
 
 import numpy as np
 
@@ -38,22 +39,25 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "synth.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libsbc_synth.so")
 _clib = None
+_lock = threading.Lock()
 
 
 def build(force: bool = False) -> str:
-    """Compile the C sampler (gcc -O2) into sbc_synth/_build/."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    """Compile the C sampler (gcc -O2) into sbc_synth/_build/ (once per
+    process; safe to call from several threads)."""
+    with _lock:
+        os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+        if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+            tmp = _LIB_PATH + f".tmp{os.getpid()}.{threading.get_ident()}"
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
 
 
 def _c():
     global _clib
     if _clib is None:
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(build())  # build() serialises the compile
         vp, i64, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
         lib.synth_chung_lu.restype = ctypes.c_int
         lib.synth_chung_lu.argtypes = [ctypes.c_uint64, i64, i64, i64, f64, f64, f64, f64, vp, vp]

@@ -91,7 +91,7 @@ def test_autotuner_choice_counts_exactly(sbc):
     try:
         t = sbc.sbc_autotune(hs, 3, 3, reps=2)
         assert t["split_per_warp"] in (0, 1, 2, 4, 8, 16)
-        assert t["small_wedges"] in (0, 64, 128, 256, 512)
+        assert t["small_wedges"] in (0, 16, 32, 48, 64)
         assert t["pos_node_cost"] in (0, 2, 4, 6, 10, 16, 64, 1 << 20)
         assert t["ms"] > 0
         with sbc.Batch(hs, 3, 3, tune=t) as b:
@@ -108,7 +108,7 @@ def test_autotuner_choice_counts_exactly(sbc):
 
 @pytest.mark.parametrize("tune", [
     {"small_wedges": 64, "pos_node_cost": 2, "split_per_warp": 16},
-    {"small_wedges": 128, "pos_node_cost": 1 << 20, "split_per_warp": 1},
+    {"small_wedges": 32, "pos_node_cost": 1 << 20, "split_per_warp": 1},
     {"small_wedges": 1, "pos_node_cost": 1, "split_per_warp": 64},
 ])
 def test_extreme_launch_parameters_exact(sbc, tune):
@@ -123,10 +123,28 @@ def test_extreme_launch_parameters_exact(sbc, tune):
 def test_launch_parameters_out_of_range_rejected(sbc):
     g = sbc_synth.plain_small()
     with sbc.graph_from_synth(g) as h:
-        for bad in [{"small_wedges": 513}, {"split_per_warp": 65}, {"pos_node_cost": -1},
+        for bad in [{"small_wedges": 65}, {"split_per_warp": 65}, {"pos_node_cost": -1},
                     {"small_wedges": -2}]:
             with pytest.raises(sbc.SbcError) as e:
                 sbc.sbc_count_ex(h, 3, 3, tune=bad)
             assert e.value.status == 1  # SBC_E_INVAL
     with pytest.raises(sbc.SbcError):
         sbc.sbc_autotune([], 3, 3)
+
+
+@pytest.mark.parametrize("index", [4829, 7100])
+def test_batch_recipe_graphs_exact(sbc, index):
+    """Two graphs of the 10,000-graph batch recipe (about 2.4e5 and 4.9e5
+    edges) whose counts once came out a few bicliques short: alone, in a
+    small batch and with every 2-hop tier threshold, against the oracle."""
+    g = sbc_synth.batch_graph(4, index)
+    want = oracle.count(g, 3, 3, side=0)
+    with sbc.graph_from_synth(g) as h:
+        assert sbc.sbc_count(h, 3, 3) == want
+        for sw in (1, 16, 64):
+            assert sbc.sbc_count_ex(h, 3, 3, tune={"small_wedges": sw})[0] == want
+        other = sbc.graph_from_synth(sbc_synth.batch_graph(4, index + 1))
+        try:
+            assert sbc.sbc_count_batch([h, other], 3, 3)[0] == want
+        finally:
+            other.close()
