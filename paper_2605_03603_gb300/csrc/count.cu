@@ -447,6 +447,10 @@ __global__ void __launch_bounds__(PS_THREADS) k_twohop_small(TwohopArgs a) {
                     uint32_t wd = i / ncw, c = i % ncw;
                     region[(size_t)wd * rsv + c] = 0;
                 }
+                // the zeroing stores of one lane must reach memory before other
+                // lanes' atomicOr on the same words (a warp barrier alone does
+                // not order plain stores against device-scope atomics)
+                __threadfence();
                 __syncwarp();
                 visit_warp(ebase, d, true, a.A_ent, a.A_pos, a.A_bit, a.B_off, a.B_ent,
                            [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
@@ -685,6 +689,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
                     uint32_t wd = i / ncw, c = i % ncw;
                     bb[(size_t)wd * bstride + c] = 0;
                 }
+                if (!staged) __threadfence();  // zeroing before other threads' atomicOr
                 __syncthreads();
                 pass2(bb, bstride);
                 __syncthreads();
