@@ -257,6 +257,53 @@ def test_tuples_metric_matches_candidate_sets():
     assert tup == sum(comb(m - 1 - i, 2) for i in range(m))
 
 
+# --- the oracle's test options: anchor subsets and the subset cap ----------------
+
+def _algorithm2_candidates(g, p, q):
+    """|C(u)| of Algorithm 2 for every U-vertex u, straight from the
+    definition: partners w with higher priority (degree, then id) sharing at
+    least q neighbours with u (dense numpy, small graphs only)."""
+    deg = np.diff(g.offsets)
+    order = np.lexsort((np.arange(g.n_u), deg))
+    rank = np.empty(g.n_u, np.int64)
+    rank[order] = np.arange(g.n_u)
+    a = np.zeros((g.n_u, g.n_v), np.int32)
+    u, v, _ = g.edges()
+    a[u, v] = 1
+    common = a @ a.T
+    higher = rank[None, :] > rank[:, None]
+    return ((common >= q) & higher).sum(axis=1)
+
+
+def test_anchor_subsets_partition_the_count():
+    g = sbc_synth.plain_small()
+    total, per = oracle.count(g, 3, 3, side=0, per_anchor=True)
+    rng = np.random.default_rng(5)
+    part = rng.integers(0, 3, g.n_u)
+    sums = 0
+    for k in range(3):
+        sub = np.nonzero(part == k)[0]
+        t, pk = oracle.count(g, 3, 3, side=0, per_anchor=True, anchors=sub)
+        assert all(pk[a] == per[a] for a in sub)
+        assert all(pk[a] == 0 for a in np.nonzero(part != k)[0])
+        sums += t
+    assert sums == total
+
+
+def test_subset_cap_skips_exactly_the_large_anchors():
+    g = sbc_synth.plain_small()
+    p, q, cap = 3, 3, 40
+    total, per = oracle.count(g, p, q, side=0, per_anchor=True)
+    skipped = set()
+    _, capped = oracle.count(g, p, q, side=0, per_anchor=True, max_subsets=cap,
+                             skipped=skipped)
+    ncand = _algorithm2_candidates(g, p, q)
+    want = {int(a) for a in range(g.n_u) if comb(int(ncand[a]), p - 1) > cap}
+    assert skipped == want and skipped
+    assert all(capped[a] == per[a] for a in range(g.n_u) if a not in skipped)
+    assert all(capped[a] == 0 for a in skipped)
+
+
 # --- the pins catch planted mistakes -------------------------------------------
 
 def _pins_pass(lib):
