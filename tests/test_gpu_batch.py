@@ -148,3 +148,23 @@ def test_batch_recipe_graphs_exact(sbc, index):
             assert sbc.sbc_count_batch([h, other], 3, 3)[0] == want
         finally:
             other.close()
+
+
+def test_two_hop_tiers_agree_on_batch_recipe(sbc):
+    """Per-graph counts of 300 graphs from the batch recipe's generator
+    (edges up to 2e5) are the same whichever 2-hop kernel takes the anchors
+    (CTA per anchor for all, or the warp kernel up to its 64-wedge cap),
+    alone and batched; small ones also against the oracle."""
+    gs = sbc_synth.batch_graphs(4, 300, 500, 200_000)
+    hs = [sbc.graph_from_synth(g) for g in gs]
+    try:
+        cta = [sbc.sbc_count_ex(h, 3, 3, tune={"small_wedges": 1})[0] for h in hs]
+        warp = [sbc.sbc_count_ex(h, 3, 3, tune={"small_wedges": 64})[0] for h in hs]
+        assert warp == cta
+        assert sbc.sbc_count_batch(hs, 3, 3) == cta
+        for i in range(0, 300, 60):
+            if gs[i].m <= 20_000:
+                assert cta[i] == oracle.count(gs[i], 3, 3, side=0)
+    finally:
+        for h in hs:
+            h.close()
