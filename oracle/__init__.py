@@ -4,14 +4,19 @@ TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
 baseline leg use it; the product path never imports it. It shares no code with
 the CUDA path.
 
-Two independent counters:
+Independent counters:
 
-* `count` -- Algorithm 2 (BBVP) of the paper, in plain C (`sbc_oracle.c`),
-  step for step in the paper's order.
-* `brute_count` -- the definition itself (Section 3, Definitions 1-4 and the
-  problem statement), in pure Python: every p-subset L of U and q-subset R of
+* `count` -- plain C (`sbc_oracle.c`): every p-subset L of U with a common
+  neighbourhood of at least q vertices, reached by a depth-first extension
+  over common neighbourhoods, adds sum over classes of binom(|class|, q),
+  the classes being the common neighbours grouped by their sign vector
+  relative to L's first member (the characterisation of a balanced biclique
+  by Lemma 1 and its converse, Section 4.2).
+* `brute_count_c` -- the definition itself (Section 3, Definitions 1-4 and
+  the problem statement) in plain C: every p-subset L of U and q-subset R of
   V, kept when L x R is complete and every butterfly in it has an even number
-  of negative edges. Tiny graphs only.
+  of negative edges. Graphs of at most 64 vertices per side.
+* `brute_count` -- the same definition in pure Python, for the tiniest cases.
 
 Convention (the problem statement takes p vertices from one partition and q
 from the other): p vertices come from U (the CSR rows) and q from V.
@@ -53,6 +58,11 @@ def _declare(lib):
         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_void_p,
         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
     ]
+    lib.sbc_oracle_brute.restype = ctypes.c_int
+    lib.sbc_oracle_brute.argtypes = [
+        ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_int, ctypes.c_int, u64p,
+    ]
     lib.sbc_oracle_binom.restype = ctypes.c_int
     lib.sbc_oracle_binom.argtypes = [ctypes.c_int64, ctypes.c_int, u64p]
     lib.sbc_oracle_max_threads.restype = ctypes.c_int
@@ -80,7 +90,8 @@ def max_threads() -> int:
 
 
 def default_side(n_u: int, n_v: int) -> int:
-    """Algorithm 2 anchors on the smaller partition S (ties: U). 0 = U, 1 = V."""
+    """Default side the sets L are drawn from: the smaller partition (ties: U),
+    as Algorithm 2 does. 0 = U, 1 = V. The count is the same either way."""
     return 0 if n_u <= n_v else 1
 
 
@@ -91,16 +102,19 @@ def _u128(lo, hi) -> int:
 def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
           per_anchor: bool = False, with_tuples: bool = False, lib=None, anchors=None,
           max_subsets: int = 0, skipped=None):
-    """Balanced (p,q)-bicliques of `g` (p from U, q from V) by Algorithm 2.
+    """Balanced (p,q)-bicliques of `g` (p from U, q from V).
 
-    side: anchor partition S (0 = U with tuple size p, 1 = V with tuple size
-    q); default the smaller partition. threads: OpenMP threads (0 = all).
-    Returns the count (int); with per_anchor, also a list of each anchor's
-    contribution (indexed by vertex id of S); with with_tuples, also the
-    number of (|S-tuple|-1)-subsets of C enumerated. anchors: optional
+    side: the partition S the sets L are drawn from (0 = U with set size p,
+    1 = V with set size q); default the smaller partition. threads: OpenMP
+    threads (0 = all). Returns the count (int); with per_anchor, also a list
+    of each anchor's share (the bicliques whose S-member of lowest priority
+    rho, Definition 4, it is; indexed by vertex id of S); with with_tuples,
+    also sum over anchors u of binom(|C(u)|, |L|-1), C(u) the vertices of
+    higher priority sharing at least the other side's size of neighbours
+    with u (the number of subsets Algorithm 2 enumerates). anchors: optional
     iterable of S-vertex ids; only those anchors are processed. max_subsets
-    (tests only): anchors with more subsets to enumerate are left out; their
-    ids are added to the set `skipped` if given.
+    (tests only): anchors with more such subsets are left out; their ids are
+    added to the set `skipped` if given.
     """
     lib = _load() if lib is None else lib
     if side is None:
@@ -136,6 +150,20 @@ def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
     if with_tuples:
         res.append(_u128(tup[0], tup[1]))
     return res[0] if len(res) == 1 else tuple(res)
+
+
+def brute_count_c(g, p: int, q: int, lib=None) -> int:
+    """The definition by brute force in C (at most 64 vertices per side)."""
+    lib = _load() if lib is None else lib
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    col = np.ascontiguousarray(g.cols, dtype=np.int32)
+    sgn = np.ascontiguousarray(g.signs, dtype=np.int8)
+    out = (ctypes.c_uint64 * 2)()
+    rc = lib.sbc_oracle_brute(g.n_u, g.n_v, off.ctypes.data, col.ctypes.data, sgn.ctypes.data,
+                              p, q, out)
+    if rc != 0:
+        raise RuntimeError(f"brute force failed with code {rc}")
+    return _u128(out[0], out[1])
 
 
 def binom(n: int, k: int) -> int:

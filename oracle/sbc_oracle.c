@@ -4,37 +4,49 @@
  *
  * TEST INFRASTRUCTURE ONLY. Nothing on the product path may call, link or
  * load this file: only the tests, the smoke check and the benchmark's CPU
- * baseline leg use it. It shares no code, header or table with the CUDA path.
+ * baseline legs use it. It shares no code, header or table with the CUDA path.
  *
- * It follows Algorithm 2 (BBVP, "vertex-based pruning", Section 4.3) of
- * "Counting Small Balanced (p,q)-bicliques in Signed Bipartite Graphs" step by
- * step, in the paper's notation:
+ * What it counts (Section 3: Definitions 1-4 and the problem statement):
+ * pairs (L, R), L a p-subset of U and R a q-subset of V, with every (x, v) in
+ * L x R an edge and no butterfly of L x R holding an odd number of negative
+ * edges.
  *
- *   for each anchor u in S:
- *     cnt[w] = number of v in Gamma(u) with w in Gamma(v), w in S, rho(w) > rho(u)
- *     C = { w : cnt[w] >= q };  skip u if |C| < p-1
- *     L[w] = Gamma(u) intersect Gamma(w)            for w in C
- *     for every (p-1)-subset A = (w_1 < ... < w_{p-1}) of C:
- *       T = intersection of L[w] over w in A;  skip if |T| < q
- *       x[kappa] = number of v in T with wedge type kappa, where
- *         c_i = s if sign(u,v) == sign(v,w_i), else d           (Section 4.2)
- *       b_pq += sum over kappa of binom(x[kappa], q)
+ * Two counters live here, written independently of each other:
  *
- * Here p is the size of the tuple drawn from the anchor side S and q the size
- * drawn from the other side. rho is the vertex priority of Definition 4
- * (degree, then id). The sum over types of binom(x[kappa], q) relies on
- * Lemma 1 (all signed p-wedges of a balanced biclique share one type) and on
- * its converse (if every v in R gives the same type, every butterfly of
- * {u, w_1..w_{p-1}} x R has an even number of negative edges); the test suite
- * pins this oracle against a brute-force check of every butterfly.
+ * sbc_oracle_brute -- the definition itself: every p-subset L of U, every
+ *   q-subset R of its common neighbourhood, every butterfly of L x R tested
+ *   for an even number of negative edges. Tiny graphs only.
+ *
+ * sbc_oracle_count -- the same number for graphs of real size, through the
+ *   sign-vector characterisation of a balanced biclique (Lemma 1 and its
+ *   converse, Section 4.2): a complete L x R is balanced exactly when every
+ *   v in R has the same sign vector relative to one fixed x1 in L, i.e. the
+ *   same bits kappa_x(v) = [sign(x1,v) != sign(x,v)] over x in L \ {x1}.
+ *   (Each butterfly (x1, x, v, v') is balanced iff kappa_x(v) = kappa_x(v');
+ *   a butterfly (x, y, v, v') without x1 has the product of the signs of
+ *   (x1,x,v,v') and (x1,y,v,v'), so it is balanced when both are.)
+ *   Hence, for a fixed L with common neighbourhood N(L), the balanced R are
+ *   the q-subsets of one class of N(L) under kappa, and the count is the sum
+ *   over L of sum over classes c of binom(|c|, q).
+ *
+ *   Every L is visited once, from its member x1 of lowest priority rho
+ *   (Definition 4: degree, then id), by a depth-first extension: a node is a
+ *   set L = {x1, ..., xd} in increasing priority together with N(L) as a list
+ *   of (v, sign(x1,v), kappa bits so far) in increasing v. Its children are
+ *   the vertices x of higher priority than xd adjacent to some v in N(L);
+ *   scanning N(L) once and appending each v to the bucket of every such x
+ *   gives each child's N(L + x) directly, in increasing v. A child with fewer
+ *   than q common neighbours has no q-subset below it (N only shrinks) and is
+ *   not visited. At |L| = p the classes of N(L) are tallied.
+ *
+ *   The anchor side S (the side L is drawn from) may be either side: the
+ *   count with p from U and q from V equals the count of the transposed
+ *   graph with q from V and p from U.
  *
  * Counts are exact: unsigned 128-bit sums, binomials by the exact
- * multiplicative formula. A binomial that would not fit 128 bits sets the
- * overflow flag.
- *
- * The loop over anchors may run on several OpenMP threads; each thread keeps
- * its own maps and partial sum, and the partial sums are added at the end
- * (integer addition, so the order does not matter).
+ * multiplicative formula; a binomial or a sum that would not fit 128 bits
+ * sets the overflow flag. The loop over anchors x1 may run on several OpenMP
+ * threads, each with its own partial sum (integer addition: order-free).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -47,9 +59,13 @@ typedef unsigned __int128 u128;
 
 /* ORACLE_MUTANT plants one known mistake (tests only, built into a separate
  * library) so that the test suite can show that its pins catch it:
- *   1 priority ties broken as "greater"   2 type from sign(w_i,v) alone
- *   3 candidates need cnt > q             4 one type class dropped
- *   5 binomial with q-1                   6 anchor included as its own partner */
+ *   1 priority compares degrees only (equal degrees admitted both ways)
+ *   2 kappa from sign(x,v) alone instead of relative to x1
+ *   3 children need more than q common neighbours
+ *   4 one class (all bits set) dropped at the leaf
+ *   5 binomial with q-1
+ *   6 a vertex may extend a set that ends with itself
+ *   7 the kappa bit of the 5th and later members lands on the 4th's bit */
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
 #endif
@@ -60,28 +76,18 @@ typedef struct {
     int8_t sign;
 } adj_t;
 
-/* L[w] entry: common neighbour v with sign(u,v) and sign(w,v). */
 typedef struct {
-    int32_t v;
-    int8_t s_uv;
-    int8_t s_wv;
-} lent_t;
-
-typedef struct {
-    int64_t n;        /* vertices on this side */
-    int64_t *off;     /* n+1 */
-    adj_t *adj;       /* off[n] entries, sorted by id within each list */
+    int64_t n;    /* vertices on this side */
+    int64_t *off; /* n+1 */
+    adj_t *adj;   /* off[n] entries */
 } side_t;
 
-static int cmp_adj(const void *a, const void *b) {
-    int32_t x = ((const adj_t *)a)->id, y = ((const adj_t *)b)->id;
-    return (x > y) - (x < y);
-}
-
-static int cmp_i32(const void *a, const void *b) {
-    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
-    return (x > y) - (x < y);
-}
+/* Entry of N(L): common neighbour v, sign(x1, v), kappa bits. */
+typedef struct {
+    int32_t v;
+    int8_t s1;
+    uint32_t kappa;
+} nent_t;
 
 static void free_side(side_t *s) {
     free(s->off);
@@ -90,63 +96,41 @@ static void free_side(side_t *s) {
     s->adj = NULL;
 }
 
-/* Adjacency of U from the CSR, each list sorted by neighbour id. */
-static int build_u_side(int64_t n_u, const int64_t *off, const int32_t *col,
-                        const int8_t *sgn, side_t *out) {
-    int64_t m = off[n_u];
-    out->n = n_u;
-    out->off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_u + 1));
+/* Transpose-style build: lists of `side` (n_side vertices) from the edge list
+ * (a[e], b[e], sgn[e]); entry of a[e] is (b[e], sign). */
+static int build_lists(int64_t n_side, int64_t m, const int32_t *a, const int32_t *b,
+                       const int8_t *sgn, side_t *out) {
+    out->n = n_side;
+    out->off = (int64_t *)calloc((size_t)(n_side + 1), sizeof(int64_t));
     out->adj = (adj_t *)malloc(sizeof(adj_t) * (size_t)(m > 0 ? m : 1));
-    if (!out->off || !out->adj) return -1;
-    for (int64_t i = 0; i <= n_u; i++) out->off[i] = off[i];
-    for (int64_t e = 0; e < m; e++) {
-        out->adj[e].id = col[e];
-        out->adj[e].sign = sgn[e];
-    }
-    for (int64_t i = 0; i < n_u; i++)
-        qsort(out->adj + off[i], (size_t)(off[i + 1] - off[i]), sizeof(adj_t), cmp_adj);
-    return 0;
-}
-
-/* Adjacency of V (the transpose), each list sorted by neighbour id. */
-static int build_v_side(int64_t n_u, int64_t n_v, const int64_t *off,
-                        const int32_t *col, const int8_t *sgn, side_t *out) {
-    int64_t m = off[n_u];
-    out->n = n_v;
-    out->off = (int64_t *)calloc((size_t)(n_v + 1), sizeof(int64_t));
-    out->adj = (adj_t *)malloc(sizeof(adj_t) * (size_t)(m > 0 ? m : 1));
-    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_v + 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_side + 1));
     if (!out->off || !out->adj || !fill) {
         free(fill);
         return -1;
     }
-    for (int64_t e = 0; e < m; e++) out->off[col[e] + 1]++;
-    for (int64_t v = 0; v < n_v; v++) out->off[v + 1] += out->off[v];
-    memcpy(fill, out->off, sizeof(int64_t) * (size_t)(n_v + 1));
-    for (int64_t u = 0; u < n_u; u++)
-        for (int64_t e = off[u]; e < off[u + 1]; e++) {
-            adj_t a;
-            a.id = (int32_t)u;
-            a.sign = sgn[e];
-            out->adj[fill[col[e]]++] = a;
-        }
+    for (int64_t e = 0; e < m; e++) out->off[a[e] + 1]++;
+    for (int64_t x = 0; x < n_side; x++) out->off[x + 1] += out->off[x];
+    memcpy(fill, out->off, sizeof(int64_t) * (size_t)(n_side + 1));
+    for (int64_t e = 0; e < m; e++) {
+        adj_t t;
+        t.id = b[e];
+        t.sign = sgn[e];
+        out->adj[fill[a[e]]++] = t;
+    }
     free(fill);
-    for (int64_t v = 0; v < n_v; v++)
-        qsort(out->adj + out->off[v], (size_t)(out->off[v + 1] - out->off[v]),
-              sizeof(adj_t), cmp_adj);
     return 0;
 }
 
-/* Definition 4: rho(a) > rho(b) iff deg(a) > deg(b), or equal degrees and
- * id(a) > id(b). */
-static int rho_greater(const side_t *s, int64_t a, int64_t b) {
-    int64_t da = s->off[a + 1] - s->off[a], db = s->off[b + 1] - s->off[b];
-    if (da != db) return da > db;
-#if ORACLE_MUTANT == 1
-    return 1;
-#else
-    return a > b;
-#endif
+/* Sorting helpers (qsort with a file-scope key array: the sorts run before
+ * any thread starts). */
+static const int64_t *g_key;
+static int cmp_by_key(const void *pa, const void *pb) {
+    int64_t x = g_key[((const adj_t *)pa)->id], y = g_key[((const adj_t *)pb)->id];
+    return (x > y) - (x < y);
+}
+static int cmp_by_id(const void *pa, const void *pb) {
+    int32_t x = ((const adj_t *)pa)->id, y = ((const adj_t *)pb)->id;
+    return (x > y) - (x < y);
 }
 
 static uint64_t gcd_u64(uint64_t a, uint64_t b) {
@@ -181,41 +165,228 @@ static u128 binom_u128(int64_t n, int k, int *ovf) {
     return r;
 }
 
-/* Section 4.2: c_i = d when sign(u,v) differs from sign(v,w_i). */
-#if ORACLE_MUTANT == 2
-#define TYPE_D(s_uv, s_wv) ((s_wv) < 0)
+/* *acc += v, flagging a sum that leaves 128 bits. */
+static void add_u128(u128 *acc, u128 v, int *ovf) {
+    u128 s = *acc + v;
+    if (s < v) *ovf = 1;
+    *acc = s;
+}
+
+/* Per-thread work space: one level of the extension per set size. */
+typedef struct {
+    nent_t *ent;  /* the children's N lists, back to back */
+    int64_t ecap;
+    int32_t *cx;  /* child vertices */
+    int64_t ccap;
+    int64_t *cb;  /* child list begins (nchild + 1) */
+    int64_t bcap;
+} level_t;
+
+typedef struct {
+    const side_t *s, *o; /* anchor side (lists by id), other side (lists by rank) */
+    const int64_t *rank; /* rank of each S vertex in rho order */
+    const int64_t *deg;  /* degree of each S vertex */
+    int p, q;            /* set size on S, subset size on the other side */
+    int32_t *mark;       /* n_S, zero between uses */
+    int32_t *touched;    /* n_S */
+    level_t lv[17];
+    u128 *xcnt;          /* class sizes, 2^(p-1) */
+    int ovf, err;
+} ctx_t;
+
+/* First entry of the other-side list `a[0..n)` (ascending rank) whose vertex
+ * may follow `last` in a set. */
+static int64_t first_later(const ctx_t *c, const adj_t *a, int64_t n, int32_t last) {
+#if ORACLE_MUTANT == 1
+    int64_t key = c->deg[last]; /* degree only: ties on both sides */
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (c->deg[a[mid].id] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 #else
-#define TYPE_D(s_uv, s_wv) ((s_uv) != (s_wv))
+    int64_t key = c->rank[last];
+#if ORACLE_MUTANT == 6
+    key -= 1; /* admits `last` itself */
 #endif
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (c->rank[a[mid].id] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+#endif
+}
 
-/* T entry: common neighbour v with the type bits gathered so far
- * (bit i set when c_i = d). */
-typedef struct {
-    int32_t v;
-    uint32_t kappa;
-} tent_t;
+static int grow(void **p, int64_t *cap, int64_t need, size_t elem) {
+    if (need <= *cap) return 0;
+    int64_t nc = *cap ? *cap : 256;
+    while (nc < need) nc *= 2;
+    void *q = realloc(*p, (size_t)nc * elem);
+    if (!q) return -1;
+    *p = q;
+    *cap = nc;
+    return 0;
+}
 
-typedef struct {
-    int32_t *cnt;      /* n_S, zero between anchors */
-    int32_t *touched;  /* ids with cnt > 0 */
-    int32_t *cand;     /* C */
-    int64_t *loff;     /* L[w] offsets, |C|+1 */
-    lent_t *lbuf;      /* L[w] lists */
-    int64_t lcap;
-    tent_t *tbuf[2];   /* T work buffers */
-    int64_t tcap;
-    u128 *xcnt;        /* x[kappa], 2^(p-1) */
-} work_t;
+/* Bit of member number d (0-based; member 0 is x1) in kappa. */
+static uint32_t kappa_bit(int d) {
+#if ORACLE_MUTANT == 7
+    if (d >= 4) return 1u << 2;
+#endif
+    return 1u << (d - 1);
+}
+
+/* Sum over the classes of N(L), |L| = p: binom(|class|, q). */
+static u128 leaf(ctx_t *c, const nent_t *n, int64_t nn) {
+    u128 b = 0;
+    uint32_t ncls = 1u << (c->p - 1);
+    for (uint32_t k = 0; k < ncls; k++) c->xcnt[k] = 0;
+    for (int64_t t = 0; t < nn; t++) c->xcnt[n[t].kappa] += 1;
+    for (uint32_t k = 0; k < ncls; k++) {
+#if ORACLE_MUTANT == 4
+        if (k == ncls - 1) continue;
+#endif
+#if ORACLE_MUTANT == 5
+        add_u128(&b, binom_u128((int64_t)c->xcnt[k], c->q - 1, &c->ovf), &c->ovf);
+#else
+        add_u128(&b, binom_u128((int64_t)c->xcnt[k], c->q, &c->ovf), &c->ovf);
+#endif
+    }
+    return b;
+}
+
+/* Children of the set whose last member is `last` (d members so far) and
+ * whose common neighbourhood is n[0..nn): fills level d with each child x and
+ * its N(L + x). Returns the number of children. */
+static int64_t children(ctx_t *c, int d, const nent_t *n, int64_t nn, int32_t last) {
+    const side_t *o = c->o;
+    level_t *L = &c->lv[d];
+    int64_t ntouch = 0;
+    /* bucket sizes */
+    for (int64_t t = 0; t < nn; t++) {
+        const adj_t *a = o->adj + o->off[n[t].v];
+        int64_t len = o->off[n[t].v + 1] - o->off[n[t].v];
+        for (int64_t f = first_later(c, a, len, last); f < len; f++) {
+            int32_t x = a[f].id;
+#if ORACLE_MUTANT == 1
+            if (x == last) continue;
+#endif
+            if (c->mark[x]++ == 0) c->touched[ntouch++] = x;
+        }
+    }
+    /* keep the children with at least q common neighbours; mark[x] becomes
+     * the child's index + 1 (0: not a child) */
+    int64_t nch = 0, tot = 0;
+    if (grow((void **)&L->cx, &L->ccap, ntouch + 1, sizeof(int32_t)) ||
+        grow((void **)&L->cb, &L->bcap, ntouch + 1, sizeof(int64_t))) {
+        c->err = 1;
+        for (int64_t i = 0; i < ntouch; i++) c->mark[c->touched[i]] = 0;
+        return 0;
+    }
+    for (int64_t i = 0; i < ntouch; i++) {
+        int32_t x = c->touched[i];
+        int32_t cnt = c->mark[x];
+#if ORACLE_MUTANT == 3
+        int keep = cnt > c->q;
+#else
+        int keep = cnt >= c->q;
+#endif
+        if (keep) {
+            L->cx[nch] = x;
+            L->cb[nch] = tot;
+            tot += cnt;
+            nch++;
+            c->mark[x] = (int32_t)nch;
+        } else {
+            c->mark[x] = 0;
+        }
+    }
+    L->cb[nch] = tot;
+    if (grow((void **)&L->ent, &L->ecap, tot + 1, sizeof(nent_t))) {
+        c->err = 1;
+        nch = 0;
+    }
+    /* fill the buckets in increasing v (n is in increasing v) */
+    if (nch > 0) {
+        int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * (size_t)nch);
+        if (!cur) {
+            c->err = 1;
+            nch = 0;
+        } else {
+            for (int64_t i = 0; i < nch; i++) cur[i] = L->cb[i];
+            uint32_t bit = kappa_bit(d);
+            for (int64_t t = 0; t < nn; t++) {
+                const adj_t *a = o->adj + o->off[n[t].v];
+                int64_t len = o->off[n[t].v + 1] - o->off[n[t].v];
+                for (int64_t f = first_later(c, a, len, last); f < len; f++) {
+                    int32_t x = a[f].id;
+                    int32_t ci = c->mark[x];
+                    if (ci == 0) continue;
+#if ORACLE_MUTANT == 1
+                    if (x == last) continue;
+#endif
+                    nent_t e = n[t];
+#if ORACLE_MUTANT == 2
+                    if (a[f].sign < 0) e.kappa |= bit;
+#else
+                    if (a[f].sign != n[t].s1) e.kappa |= bit;
+#endif
+                    L->ent[cur[ci - 1]++] = e;
+                }
+            }
+            free(cur);
+        }
+    }
+    for (int64_t i = 0; i < ntouch; i++) c->mark[c->touched[i]] = 0;
+    return nch;
+}
+
+/* Balanced bicliques of the sets extending L (d members, last member `last`,
+ * common neighbourhood n[0..nn)). */
+static u128 extend(ctx_t *c, int d, const nent_t *n, int64_t nn, int32_t last) {
+    if (d == c->p) return leaf(c, n, nn);
+    int64_t nch = children(c, d, n, nn, last);
+    level_t *L = &c->lv[d];
+    u128 b = 0;
+    for (int64_t i = 0; i < nch && !c->err; i++)
+        add_u128(&b, extend(c, d + 1, L->ent + L->cb[i], L->cb[i + 1] - L->cb[i], L->cx[i]),
+                 &c->ovf);
+    return b;
+}
 
 /*
- * Algorithm 2 on anchor side S (adjacency `s`), other side `o`.
- * p = tuple size on S, q = size on the other side.
+ * Count on anchor side S (lists `s`, by id) against the other side `o`.
+ * p = set size on S, q = subset size on the other side.
  */
-static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
-                const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped,
-                uint64_t out[2], uint64_t *anchor_out, uint64_t *tuples_out, int *ovf_out) {
+static int count_side(const side_t *s, side_t *o, int p, int q, int nthreads,
+                      const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped,
+                      uint64_t out[2], uint64_t *anchor_out, uint64_t *tuples_out, int *ovf_out) {
     int64_t nS = s->n;
-    int ovf = 0;
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nS > 0 ? nS : 1));
+    int64_t *rank = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nS > 0 ? nS : 1));
+    adj_t *ord = (adj_t *)malloc(sizeof(adj_t) * (size_t)(nS > 0 ? nS : 1));
+    int64_t *key = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nS > 0 ? nS : 1));
+    if (!deg || !rank || !ord || !key) {
+        free(deg), free(rank), free(ord), free(key);
+        return -1;
+    }
+    /* Definition 4: rho orders by degree, then by id */
+    for (int64_t x = 0; x < nS; x++) {
+        deg[x] = s->off[x + 1] - s->off[x];
+        key[x] = deg[x] * (nS + 1) + x;
+        ord[x].id = (int32_t)x;
+    }
+    g_key = key;
+    qsort(ord, (size_t)nS, sizeof(adj_t), cmp_by_key);
+    for (int64_t i = 0; i < nS; i++) rank[ord[i].id] = i;
+    /* the other side's lists in increasing rank, the anchor side's by id */
+    for (int64_t v = 0; v < o->n; v++)
+        qsort(o->adj + o->off[v], (size_t)(o->off[v + 1] - o->off[v]), sizeof(adj_t), cmp_by_key);
+    free(ord);
+    free(key);
+
     int nt = 1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -225,17 +396,8 @@ static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
 #endif
     u128 *part = (u128 *)calloc((size_t)nt, sizeof(u128));
     u128 *tup = (u128 *)calloc((size_t)nt, sizeof(u128));
-    int err = 0;
-    if (!part || !tup) {
-        free(part);
-        free(tup);
-        return -1;
-    }
-    int64_t maxdeg = 0;
-    for (int64_t u = 0; u < nS; u++) {
-        int64_t d = s->off[u + 1] - s->off[u];
-        if (d > maxdeg) maxdeg = d;
-    }
+    int ovf = 0, err = 0;
+    if (!part || !tup) err = 1;
 
 #pragma omp parallel reduction(| : ovf, err)
     {
@@ -243,181 +405,81 @@ static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        work_t w;
-        memset(&w, 0, sizeof(w));
-        w.cnt = (int32_t *)calloc((size_t)(nS > 0 ? nS : 1), sizeof(int32_t));
-        w.touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nS > 0 ? nS : 1));
-        w.cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nS > 0 ? nS : 1));
-        w.loff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nS + 1));
-        w.lcap = 1024;
-        w.lbuf = (lent_t *)malloc(sizeof(lent_t) * (size_t)w.lcap);
-        w.tcap = maxdeg + 1;
-        w.tbuf[0] = (tent_t *)malloc(sizeof(tent_t) * (size_t)w.tcap);
-        w.tbuf[1] = (tent_t *)malloc(sizeof(tent_t) * (size_t)w.tcap);
-        w.xcnt = (u128 *)malloc(sizeof(u128) * ((size_t)1 << (p - 1)));
-        int *idx = (int *)malloc(sizeof(int) * (size_t)p);
-        if (!w.cnt || !w.touched || !w.cand || !w.loff || !w.lbuf || !w.tbuf[0] ||
-            !w.tbuf[1] || !w.xcnt || !idx)
-            err = 1;
+        ctx_t c;
+        memset(&c, 0, sizeof(c));
+        c.s = s;
+        c.o = o;
+        c.rank = rank;
+        c.deg = deg;
+        c.p = p;
+        c.q = q;
+        c.mark = (int32_t *)calloc((size_t)(nS > 0 ? nS : 1), sizeof(int32_t));
+        c.touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nS > 0 ? nS : 1));
+        c.xcnt = (u128 *)malloc(sizeof(u128) * ((size_t)1 << (p - 1)));
+        nent_t *n1 = NULL;
+        int64_t n1cap = 0;
+        if (!c.mark || !c.touched || !c.xcnt || err) c.err = 1;
 
 #pragma omp for schedule(dynamic, 16)
         for (int64_t u = 0; u < nS; u++) {
-            if (err) continue;
+            if (c.err) continue;
             if (anchor_mask && !anchor_mask[u]) continue; /* test subset of anchors */
-            u128 b_u = 0;       /* this anchor's contribution */
-            u128 tuples_u = 0;  /* (p-1)-subsets of C enumerated */
-            int64_t nt_touch = 0;
-            /* cnt[w]: shared neighbours of u and w, rho(w) > rho(u) */
-            for (int64_t e = s->off[u]; e < s->off[u + 1]; e++) {
-                int32_t v = s->adj[e].id;
-                for (int64_t f = o->off[v]; f < o->off[v + 1]; f++) {
-                    int32_t x = o->adj[f].id;
-#if ORACLE_MUTANT == 6
-                    if (x != u && !rho_greater(s, x, u)) continue;
-#else
-                    if (x == u || !rho_greater(s, x, u)) continue;
-#endif
-                    if (w.cnt[x]++ == 0) w.touched[nt_touch++] = x;
-                }
+            /* N({u}) = Gamma(u), in increasing v */
+            int64_t du = s->off[u + 1] - s->off[u];
+            if (grow((void **)&n1, &n1cap, du + 1, sizeof(nent_t))) {
+                c.err = 1;
+                continue;
             }
-            /* C = { w : cnt[w] >= q } (necessary pairwise condition) */
-            int64_t nc = 0;
-            for (int64_t i = 0; i < nt_touch; i++)
-#if ORACLE_MUTANT == 3
-                if (w.cnt[w.touched[i]] > q) w.cand[nc++] = w.touched[i];
-#else
-                if (w.cnt[w.touched[i]] >= q) w.cand[nc++] = w.touched[i];
-#endif
-            for (int64_t i = 0; i < nt_touch; i++) w.cnt[w.touched[i]] = 0;
-            if (nc >= p - 1 && max_subsets) {
-                /* test option: leave out anchors with too many subsets */
+            for (int64_t e = 0; e < du; e++) {
+                n1[e].v = s->adj[s->off[u] + e].id;
+                n1[e].s1 = s->adj[s->off[u] + e].sign;
+                n1[e].kappa = 0;
+            }
+            u128 b_u = 0, tuples_u = 0;
+            {
+                int64_t nch = children(&c, 1, n1, du, (int32_t)u);
+                /* the (p-1)-subsets of u's first-level children are the sets
+                 * Algorithm 2 enumerates for anchor u (reported, not used) */
                 int dummy = 0;
-                if (binom_u128(nc, p - 1, &dummy) > (u128)max_subsets || dummy) {
+                tuples_u = binom_u128(nch, p - 1, &dummy);
+                if (max_subsets && (tuples_u > (u128)max_subsets || dummy)) {
+                    /* test option: leave out anchors with too many subsets */
                     if (skipped) skipped[u] = 1;
-                    nc = 0;
+                    nch = 0;
                 }
+                level_t *L = &c.lv[1];
+                for (int64_t i = 0; i < nch && !c.err; i++)
+                    add_u128(&b_u, extend(&c, 2, L->ent + L->cb[i], L->cb[i + 1] - L->cb[i], L->cx[i]),
+                             &c.ovf);
             }
-            if (nc >= p - 1) {
-                /* w_1 < ... < w_{p-1}: order C by vertex id */
-                qsort(w.cand, (size_t)nc, sizeof(int32_t), cmp_i32);
-                /* L[w] = Gamma(u) intersect Gamma(w), sorted by v */
-                int64_t du = s->off[u + 1] - s->off[u];
-                if (w.lcap < nc * du) {
-                    free(w.lbuf);
-                    w.lcap = nc * du;
-                    w.lbuf = (lent_t *)malloc(sizeof(lent_t) * (size_t)w.lcap);
-                    if (!w.lbuf) {
-                        err = 1;
-                        continue;
-                    }
-                }
-                int64_t pos = 0;
-                for (int64_t c = 0; c < nc; c++) {
-                    int32_t x = w.cand[c];
-                    w.loff[c] = pos;
-                    int64_t a = s->off[u], ae = s->off[u + 1];
-                    int64_t bb = s->off[x], be = s->off[x + 1];
-                    while (a < ae && bb < be) {
-                        if (s->adj[a].id < s->adj[bb].id) a++;
-                        else if (s->adj[a].id > s->adj[bb].id) bb++;
-                        else {
-                            w.lbuf[pos].v = s->adj[a].id;
-                            w.lbuf[pos].s_uv = s->adj[a].sign;
-                            w.lbuf[pos].s_wv = s->adj[bb].sign;
-                            pos++;
-                            a++;
-                            bb++;
-                        }
-                    }
-                }
-                w.loff[nc] = pos;
-                /* every (p-1)-subset A of C, as increasing index tuples */
-                int k = p - 1;
-                for (int i = 0; i < k; i++) idx[i] = i;
-                for (;;) {
-                    tuples_u += 1;
-                    /* T = intersection of L[w_i] over A, each v carrying its
-                     * type bits: bit i set when c_i = d, i.e.
-                     * sign(u,v) != sign(v,w_i) */
-                    int64_t tn = 0;
-                    tent_t *cur = w.tbuf[0], *nxt = w.tbuf[1];
-                    {
-                        const lent_t *l1 = w.lbuf + w.loff[idx[0]];
-                        int64_t ln = w.loff[idx[0] + 1] - w.loff[idx[0]];
-                        for (int64_t t = 0; t < ln; t++) {
-                            cur[tn].v = l1[t].v;
-                            cur[tn].kappa = TYPE_D(l1[t].s_uv, l1[t].s_wv) ? 1u : 0u;
-                            tn++;
-                        }
-                    }
-                    for (int i = 1; i < k; i++) {
-                        const lent_t *lw = w.lbuf + w.loff[idx[i]];
-                        int64_t ln = w.loff[idx[i] + 1] - w.loff[idx[i]];
-                        int64_t a = 0, bb = 0, nn = 0;
-                        while (a < tn && bb < ln) {
-                            if (cur[a].v < lw[bb].v) a++;
-                            else if (cur[a].v > lw[bb].v) bb++;
-                            else {
-                                nxt[nn].v = cur[a].v;
-                                nxt[nn].kappa = cur[a].kappa |
-                                    (TYPE_D(lw[bb].s_uv, lw[bb].s_wv) ? (1u << i) : 0u);
-                                nn++;
-                                a++;
-                                bb++;
-                            }
-                        }
-                        tent_t *t = cur;
-                        cur = nxt;
-                        nxt = t;
-                        tn = nn;
-                    }
-                    if (tn >= q) {
-                        /* x[kappa] counts, then sum of binom(x[kappa], q) */
-                        for (uint32_t kk = 0; kk < (1u << k); kk++) w.xcnt[kk] = 0;
-                        for (int64_t t = 0; t < tn; t++) w.xcnt[cur[t].kappa] += 1;
-                        for (uint32_t kk = 0; kk < (1u << k); kk++) {
-#if ORACLE_MUTANT == 4
-                            if (kk == (1u << k) - 1) continue;
-#endif
-#if ORACLE_MUTANT == 5
-                            b_u += binom_u128((int64_t)w.xcnt[kk], q - 1, &ovf);
-#else
-                            b_u += binom_u128((int64_t)w.xcnt[kk], q, &ovf);
-#endif
-                        }
-                    }
-                    /* next subset */
-                    int i = k - 1;
-                    while (i >= 0 && idx[i] == nc - k + i) i--;
-                    if (i < 0) break;
-                    idx[i]++;
-                    for (int j = i + 1; j < k; j++) idx[j] = idx[j - 1] + 1;
-                }
-            }
-            part[tid] += b_u;
+            add_u128(&part[tid], b_u, &c.ovf);
             tup[tid] += tuples_u;
             if (anchor_out) {
                 anchor_out[2 * u] = (uint64_t)b_u;
                 anchor_out[2 * u + 1] = (uint64_t)(b_u >> 64);
             }
         }
-        free(w.cnt);
-        free(w.touched);
-        free(w.cand);
-        free(w.loff);
-        free(w.lbuf);
-        free(w.tbuf[0]);
-        free(w.tbuf[1]);
-        free(w.xcnt);
-        free(idx);
+        ovf |= c.ovf;
+        err |= c.err;
+        free(c.mark);
+        free(c.touched);
+        free(c.xcnt);
+        free(n1);
+        for (int d = 0; d < 17; d++) {
+            free(c.lv[d].ent);
+            free(c.lv[d].cx);
+            free(c.lv[d].cb);
+        }
     }
     u128 total = 0, tt = 0;
-    for (int i = 0; i < nt; i++) {
-        total += part[i];
+    for (int i = 0; i < nt && part; i++) {
+        add_u128(&total, part[i], &ovf);
         tt += tup[i];
     }
     free(part);
     free(tup);
+    free(deg);
+    free(rank);
     out[0] = (uint64_t)total;
     out[1] = (uint64_t)(total >> 64);
     if (tuples_out) {
@@ -428,43 +490,140 @@ static int bbvp(const side_t *s, const side_t *o, int p, int q, int nthreads,
     return err ? -1 : 0;
 }
 
+/* Edge arrays of a CSR over U, checked: offsets from 0, non-decreasing, ids
+ * in range, signs +1/-1. */
+static int edges_of(int64_t n_u, int64_t n_v, const int64_t *off, const int32_t *col,
+                    const int8_t *sgn, int32_t **ru) {
+    if (off[0] != 0) return -2;
+    int64_t m = off[n_u];
+    *ru = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    if (!*ru) return -1;
+    for (int64_t u = 0; u < n_u; u++) {
+        if (off[u + 1] < off[u]) return -2;
+        for (int64_t e = off[u]; e < off[u + 1]; e++) {
+            if (col[e] < 0 || col[e] >= n_v || (sgn[e] != 1 && sgn[e] != -1)) return -2;
+            (*ru)[e] = (int32_t)u;
+        }
+    }
+    return 0;
+}
+
 /*
  * Count balanced bicliques with p_u vertices from U and q_v from V.
- *   anchor_side 0: S = U (tuple size p_u, other size q_v)
- *   anchor_side 1: S = V (tuple size q_v, other size p_u)
+ *   anchor_side 0: L drawn from U (set size p_u, subsets of V of size q_v)
+ *   anchor_side 1: L drawn from V (set size q_v, subsets of U of size p_u)
  * off/col/sgn: CSR over U, signs +1/-1. out: u128 total as {lo, hi}.
- * anchor_out (optional): per-anchor contribution, 2 u64 per vertex of S.
- * tuples_out (optional): number of (p-1)-subsets enumerated, {lo, hi}.
- * anchor_mask (optional): one byte per vertex of S; only anchors with a
- * non-zero byte are processed (the total then covers those anchors only).
- * max_subsets (test option, 0 = none): anchors whose (p-1)-subsets of C
- * number more are left out and flagged in `skipped` (one byte per vertex).
+ * anchor_out (optional): each anchor's share (the sets whose member of lowest
+ * priority it is), 2 u64 per vertex of the anchor side.
+ * tuples_out (optional): sum over anchors u of binom(|C(u)|, p-1), C(u) the
+ * vertices of higher priority sharing at least q neighbours with u (the
+ * number of subsets Algorithm 2 enumerates), {lo, hi}.
+ * anchor_mask (optional): one byte per anchor-side vertex; only anchors with
+ * a non-zero byte are processed (the total then covers those anchors only).
+ * max_subsets (test option, 0 = none): anchors whose binom(|C(u)|, p-1)
+ * exceeds it are left out and flagged in `skipped` (one byte per vertex).
  * Returns 0, -1 on allocation failure, -2 on bad arguments, 1 on overflow.
  */
-int sbc_oracle_count(int64_t n_u, int64_t n_v, const int64_t *off,
-                     const int32_t *col, const int8_t *sgn, int p_u, int q_v,
-                     int anchor_side, int nthreads, uint64_t out[2],
-                     uint64_t *anchor_out, uint64_t *tuples_out,
+int sbc_oracle_count(int64_t n_u, int64_t n_v, const int64_t *off, const int32_t *col,
+                     const int8_t *sgn, int p_u, int q_v, int anchor_side, int nthreads,
+                     uint64_t out[2], uint64_t *anchor_out, uint64_t *tuples_out,
                      const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped) {
-    if (p_u < 2 || q_v < 2 || p_u > 16 || q_v > 16 || n_u < 0 || n_v < 0) return -2;
+    if (p_u < 2 || q_v < 2 || p_u > 16 || q_v > 16 || n_u < 0 || n_v < 0 || n_u >= INT32_MAX ||
+        n_v >= INT32_MAX)
+        return -2;
+    int32_t *ru = NULL;
+    int rc = edges_of(n_u, n_v, off, col, sgn, &ru);
+    if (rc) {
+        free(ru);
+        return rc;
+    }
+    int64_t m = off[n_u];
     side_t su, sv;
     memset(&su, 0, sizeof(su));
     memset(&sv, 0, sizeof(sv));
-    if (build_u_side(n_u, off, col, sgn, &su) || build_v_side(n_u, n_v, off, col, sgn, &sv)) {
+    if (build_lists(n_u, m, ru, col, sgn, &su) || build_lists(n_v, m, col, ru, sgn, &sv)) {
+        free(ru);
         free_side(&su);
         free_side(&sv);
         return -1;
     }
-    int ovf = 0, rc;
+    free(ru);
+    side_t *s = anchor_side == 0 ? &su : &sv, *o = anchor_side == 0 ? &sv : &su;
+    for (int64_t x = 0; x < s->n; x++)
+        qsort(s->adj + s->off[x], (size_t)(s->off[x + 1] - s->off[x]), sizeof(adj_t), cmp_by_id);
+    int ovf = 0;
     if (anchor_side == 0)
-        rc = bbvp(&su, &sv, p_u, q_v, nthreads, anchor_mask, max_subsets, skipped, out,
-                  anchor_out, tuples_out, &ovf);
+        rc = count_side(s, o, p_u, q_v, nthreads, anchor_mask, max_subsets, skipped, out,
+                        anchor_out, tuples_out, &ovf);
     else
-        rc = bbvp(&sv, &su, q_v, p_u, nthreads, anchor_mask, max_subsets, skipped, out,
-                  anchor_out, tuples_out, &ovf);
+        rc = count_side(s, o, q_v, p_u, nthreads, anchor_mask, max_subsets, skipped, out,
+                        anchor_out, tuples_out, &ovf);
     free_side(&su);
     free_side(&sv);
     if (rc) return rc;
+    return ovf ? 1 : 0;
+}
+
+/* Next k-subset of {0..n-1} in lexicographic order; 0 when done. */
+static int next_subset(int *idx, int k, int n) {
+    int i = k - 1;
+    while (i >= 0 && idx[i] == n - k + i) i--;
+    if (i < 0) return 0;
+    idx[i]++;
+    for (int j = i + 1; j < k; j++) idx[j] = idx[j - 1] + 1;
+    return 1;
+}
+
+/*
+ * The definition, by brute force (tiny graphs: n_u, n_v <= 64): every
+ * p-subset L of U, every q-subset R of V with L x R complete, kept when every
+ * butterfly (x, y, v, w) of L x R has an even number of negative edges.
+ * Returns 0, -2 on bad arguments or sizes, 1 on overflow.
+ */
+int sbc_oracle_brute(int64_t n_u, int64_t n_v, const int64_t *off, const int32_t *col,
+                     const int8_t *sgn, int p, int q, uint64_t out[2]) {
+    if (p < 1 || q < 1 || p > 64 || q > 64 || n_u < 0 || n_v < 0 || n_u > 64 || n_v > 64)
+        return -2;
+    /* sign matrix: 0 = no edge */
+    int8_t S[64][64];
+    memset(S, 0, sizeof(S));
+    for (int64_t u = 0; u < n_u; u++)
+        for (int64_t e = off[u]; e < off[u + 1]; e++) {
+            if (col[e] < 0 || col[e] >= n_v || (sgn[e] != 1 && sgn[e] != -1)) return -2;
+            S[u][col[e]] = sgn[e];
+        }
+    u128 total = 0;
+    int ovf = 0;
+    if (p <= n_u && q <= n_v) {
+        int L[64], R[64], C[64];
+        for (int i = 0; i < p; i++) L[i] = i;
+        do {
+            /* the columns adjacent to every row of L */
+            int nc = 0;
+            for (int v = 0; v < n_v; v++) {
+                int all = 1;
+                for (int i = 0; i < p; i++)
+                    if (!S[L[i]][v]) all = 0;
+                if (all) C[nc++] = v;
+            }
+            if (nc < q) continue;
+            for (int j = 0; j < q; j++) R[j] = j;
+            do {
+                int ok = 1;
+                for (int a = 0; a < p && ok; a++)
+                    for (int b = a + 1; b < p && ok; b++)
+                        for (int c = 0; c < q && ok; c++)
+                            for (int d = c + 1; d < q && ok; d++) {
+                                int neg = (S[L[a]][C[R[c]]] < 0) + (S[L[a]][C[R[d]]] < 0) +
+                                          (S[L[b]][C[R[c]]] < 0) + (S[L[b]][C[R[d]]] < 0);
+                                if (neg & 1) ok = 0;
+                            }
+                if (ok) add_u128(&total, 1, &ovf);
+            } while (next_subset(R, q, nc));
+        } while (next_subset(L, p, (int)n_u));
+    }
+    out[0] = (uint64_t)total;
+    out[1] = (uint64_t)(total >> 64);
     return ovf ? 1 : 0;
 }
 

@@ -1,10 +1,12 @@
 """Pins for the CPU oracle (no GPU).
 
-The oracle (`oracle.count`, Algorithm 2 in C) and the brute force
-(`oracle.brute_count`, the definition of Section 3) are checked against facts
-that do not come from either: the butterflies of Figure 2, the worked example
-of Figure 3, a hand-derived count on Figure 1(b), closed forms on complete
-bipartite graphs, the (2,q) pair formula, exact binomials and invariances.
+The oracle (`oracle.count`, a depth-first count over common neighbourhoods in
+C) and the brute forces (`oracle.brute_count` in Python and
+`oracle.brute_count_c` in C, the definition of Section 3) are checked against
+facts that do not come from either: the butterflies of Figure 2, the worked
+example of Figure 3, a hand-derived count on Figure 1(b), closed forms on
+complete bipartite graphs up to (p,q) = (8,8), the (2,q) pair formula, exact
+binomials and invariances.
 Each pin is chosen so that a plausible slip (ties in the vertex priority, a
 wrong sign relation, a dropped binomial term, a transposed side) fails it.
 """
@@ -75,7 +77,10 @@ def test_fig3_per_anchor():
     # id 1 < id 2), etc.; per-anchor values must add up to the total.
     total, per = oracle.count(g, 3, 2, side=0, per_anchor=True)
     assert total == 3 and sum(per) == 3
-    assert per[0] == 0  # u1 has the highest priority, never an anchor here
+    # {u1,u2,u3} -> {v1,v2} and {u1,u2,u4} -> {v1,v3} are anchored at u2,
+    # {u1,u3,u4} -> {v1,v4} at u3; u1 (degree 4) and u4 (highest id among
+    # the degree-3 vertices) anchor none
+    assert per == [0, 2, 1, 0]
 
 
 # --- Figure 1(b): hand-derived count ----------------------------------------
@@ -128,6 +133,72 @@ def test_complete_one_negative_edge(m, n, us, vs):
         assert oracle.brute_count(g, p, q) == want
 
 
+# Signed closed forms up to (8,8). On K_{m,n} with all edges positive except
+# chosen special rows x whose edges to a column set B_x are negative, a
+# column set R is balanced with row set L when every butterfly has an even
+# number of negative edges, i.e. when the rows' sign vectors on R agree up
+# to one global flip. Group L's rows: T = its special rows. If L also holds
+# an ordinary row (all +1 on R), every special row must be constant on R:
+# R lies in one cell of V under membership in the B_x, x in T. If L = T, the
+# membership vectors of R's columns must agree up to complement. Summing
+# over T (binom(m - #specials, p - |T|) choices of the ordinary rows) gives
+# the count.
+
+def special_rows_graph(m, n, patterns):
+    """K_{m,n}, rows listed in `patterns` (row -> set of columns) negative
+    on their set."""
+    return complete(m, n, lambda u, v: -1 if v in patterns.get(u, ()) else 1)
+
+
+def special_rows_count(m, n, patterns, p, q):
+    spec = sorted(patterns)
+    total = 0
+    for t in range(len(spec) + 1):
+        for T in itertools.combinations(spec, t):
+            if p - t < 0:
+                continue
+            cells = {}
+            for v in range(n):
+                key = tuple(v in patterns[x] for x in T)
+                if p == t and key and key[0]:  # no ordinary row: up to complement
+                    key = tuple(not b for b in key)
+                cells[key] = cells.get(key, 0) + 1
+            total += comb(m - len(spec), p - t) * sum(comb(c, q) for c in cells.values())
+    return total
+
+
+@pytest.mark.parametrize("p,q", [(5, 7), (8, 8), (6, 5), (7, 3), (4, 8), (2, 8)])
+def test_signed_closed_forms_large_pq(p, q):
+    m, n = 10, 11
+    # one negative edge
+    us, vs = m - 1, 4
+    g1 = complete(m, n, lambda u, v: -1 if (u, v) == (us, vs) else 1)
+    want1 = comb(m, p) * comb(n, q) - comb(m - 1, p - 1) * comb(n - 1, q - 1)
+    # planted factions, no flips (switching-equivalent to all positive)
+    rng = random.Random(p * 10 + q)
+    lu = [rng.choice((1, -1)) for _ in range(m)]
+    lv = [rng.choice((1, -1)) for _ in range(n)]
+    g2 = complete(m, n, lambda u, v: lu[u] * lv[v])
+    want2 = comb(m, p) * comb(n, q)
+    # three special rows with the highest ids (the last members of every set
+    # that holds them), patterns cutting V into up to 8 cells
+    pats = {m - 3: {0, 1, 2, 3, 4, 5}, m - 2: {0, 1, 2, 6, 7}, m - 1: {0, 3, 6, 8, 9}}
+    g3 = special_rows_graph(m, n, pats)
+    want3 = special_rows_count(m, n, pats, p, q)
+    for g, want in ((g1, want1), (g2, want2), (g3, want3)):
+        for side in (0, 1):
+            assert oracle.count(g, p, q, side=side) == want, (side, want)
+
+
+def test_special_rows_formula_against_brute_force():
+    """The special-rows formula itself, against the butterfly-by-butterfly
+    definition on graphs small enough for it."""
+    pats = {4: {0, 1, 2}, 5: {0, 3}, 6: {1, 3, 5}}
+    g = special_rows_graph(7, 7, pats)
+    for p, q in [(2, 2), (3, 3), (4, 2), (5, 3), (6, 2), (7, 2), (3, 5)]:
+        assert oracle.brute_count_c(g, p, q) == special_rows_count(7, 7, pats, p, q)
+
+
 # --- (2,q): balanced bicliques through a vertex pair --------------------------
 
 def pair_formula(g, q):
@@ -153,6 +224,41 @@ def test_pair_formula(seed):
 
 
 # --- brute force on random tiny graphs ---------------------------------------
+
+@pytest.mark.parametrize("seed", range(10))
+def test_brute_force_c_equals_python(seed):
+    rng = random.Random(1000 + seed)
+    g = sbc_synth.tiny_random(500 + seed, rng.randint(2, 6), rng.randint(2, 6),
+                              rng.uniform(0.5, 1.0), rng.uniform(0.0, 0.5))
+    for p in range(2, 5):
+        for q in range(2, 5):
+            assert oracle.brute_count_c(g, p, q) == oracle.brute_count(g, p, q), (p, q)
+
+
+def faction_graph(seed, n_u, n_v, density, flip):
+    """Dense graph with planted two-faction signs and a few flipped edges, so
+    that large balanced bicliques exist and the flips split their classes."""
+    rng = random.Random(seed)
+    lu = [rng.choice((1, -1)) for _ in range(n_u)]
+    lv = [rng.choice((1, -1)) for _ in range(n_v)]
+    uu, vv, ss = [], [], []
+    for u in range(n_u):
+        for v in range(n_v):
+            if rng.random() < density:
+                uu.append(u)
+                vv.append(v)
+                ss.append(lu[u] * lv[v] * (-1 if rng.random() < flip else 1))
+    return sbc_synth.from_edges(n_u, n_v, uu, vv, ss)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_brute_force_large_pq_on_10x10(seed):
+    """(p,q) up to (5,5) and (6,4) on 10 x 10 graphs, against the definition."""
+    g = faction_graph(seed, 10, 10, 0.92, 0.06)
+    for p, q in [(5, 5), (4, 5), (5, 3), (6, 4), (3, 6)]:
+        want = oracle.brute_count_c(g, p, q)
+        assert oracle.count(g, p, q, side=0) == want, (p, q)
+        assert oracle.count(g, p, q, side=1) == want, (p, q)
 
 @pytest.mark.parametrize("seed", range(40))
 def test_brute_force_random_tiny(seed):
@@ -327,6 +433,14 @@ def _pins_pass(lib):
             for side in (0, 1):
                 if oracle.count(t, p, q, side=side, lib=lib) != want:
                     return False
+    pats = {7: {0, 1, 2, 3, 4, 5}, 8: {0, 1, 2, 6, 7}, 9: {0, 3, 6, 8, 9}}
+    h = special_rows_graph(10, 11, pats)
+    for p, q in [(6, 3), (8, 2)]:
+        if oracle.count(h, p, q, side=0, lib=lib) != special_rows_count(10, 11, pats, p, q):
+            return False
+    t = faction_graph(3, 10, 10, 0.92, 0.06)
+    if oracle.count(t, 5, 5, side=0, lib=lib) != oracle.brute_count_c(t, 5, 5):
+        return False
     return True
 
 
@@ -334,7 +448,7 @@ def test_pins_pass_on_oracle():
     assert _pins_pass(None)
 
 
-@pytest.mark.parametrize("mutant", range(1, 7))
+@pytest.mark.parametrize("mutant", range(1, 8))
 def test_pins_catch_planted_mistakes(mutant, tmp_path):
     lib = oracle.mutant(mutant, str(tmp_path))
     assert not _pins_pass(lib)
