@@ -120,6 +120,11 @@ sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
 #define SBC_COUNT_CANDIDATE_SIDE (1 << 1) /* enumerate candidate subsets for every anchor */
 #define SBC_COUNT_POSITION_SIDE (1 << 2)  /* enumerate position subsets wherever they fit
                                              (default: the cheaper side per anchor) */
+#define SBC_COUNT_CHECK (1 << 3) /* device self-checks: after the 2-hop step every kept
+                                    candidate's mask popcounts are compared with the
+                                    counters of its hash-table entry; a mismatch gives
+                                    SBC_E_CUDA. Also enabled for every count by the
+                                    environment variable SBC_DEBUG=1. Slower. */
 
 /*
  * Launch parameters of the counting kernels: the search space of the
@@ -128,7 +133,7 @@ sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
  *   small_wedges   anchors whose 2-hop visit (Algorithm 2's cnt loop) covers
  *                  at most this many wedges take the warp-per-anchor 2-hop
  *                  kernel; the others take a whole CTA of 16 warps each.
- *                  1..64, default 64.
+ *                  1..512, default 512.
  *   pos_node_cost  cost of one prefix node of the position-side enumeration
  *                  relative to one word test of the candidate-side
  *                  enumeration; each anchor takes the cheaper side, so a
@@ -239,7 +244,7 @@ sbc_status sbc_batch_destroy(sbc_batch *b);
  * single graph is a batch of one) for (p, q) under candidate launch
  * parameters and writes the fastest to *out (out->ms = its time per count).
  * The search is coordinate descent from the defaults over split_per_warp
- * {1, 2, 4, 8, 16}, small_wedges {16, 32, 48, 64} and pos_node_cost
+ * {1, 2, 4, 8, 16}, small_wedges {32, 64, 128, 256, 512} and pos_node_cost
  * {2, 4, 6, 10, 16, 64, 2^20}; each candidate is planned once and its
  * counting kernels timed (best of `reps`, 0 = 3) with CUDA events on
  * `stream`. Every candidate must produce the same counts, or the call fails

@@ -41,6 +41,7 @@ SBC_SIDE_AUTO, SBC_SIDE_U, SBC_SIDE_V = -1, 0, 1
 SBC_COUNT_PAPER_TUPLES = 1
 SBC_COUNT_CANDIDATE_SIDE = 2
 SBC_COUNT_POSITION_SIDE = 4
+SBC_COUNT_CHECK = 8
 
 STATUS = {0: "SBC_OK", 1: "SBC_E_INVAL", 2: "SBC_E_GRAPH", 3: "SBC_E_NOMEM", 4: "SBC_E_CUDA",
           5: "SBC_E_TIMEOUT", 6: "SBC_E_BUSY", 7: "SBC_E_UNSUPPORTED", 8: "SBC_E_OVERFLOW"}
@@ -301,11 +302,13 @@ def sbc_count(g: Graph, p: int, q: int, stream=None) -> int:
 
 def sbc_count_ex(g: Graph, p: int, q: int, anchor_side: int = SBC_SIDE_AUTO,
                  per_anchor: bool = False, paper_tuples: bool = False, shard: int = 0,
-                 shard_count: int = 0, method: str = "auto", tune=None, stream=None):
+                 shard_count: int = 0, method: str = "auto", tune=None, stream=None,
+                 check: bool = False):
     """sbc_count_ex: returns (count, stats dict, per-anchor list or None).
     method: "auto" (cheaper side per anchor), "candidate" or "position".
     tune: launch parameters (a dict with sbc_tune_t's fields, e.g. from
-    sbc_autotune, or None for the defaults)."""
+    sbc_autotune, or None for the defaults). check: device self-checks
+    (SBC_COUNT_CHECK)."""
     opts = CountOpts()
     t = _tune(tune)
     if t is not None:
@@ -313,6 +316,8 @@ def sbc_count_ex(g: Graph, p: int, q: int, anchor_side: int = SBC_SIDE_AUTO,
     opts.anchor_side = anchor_side
     opts.flags = (SBC_COUNT_PAPER_TUPLES if paper_tuples else 0) | {
         "auto": 0, "candidate": SBC_COUNT_CANDIDATE_SIDE, "position": SBC_COUNT_POSITION_SIDE}[method]
+    if check:
+        opts.flags |= SBC_COUNT_CHECK
     opts.shard = shard
     opts.shard_count = shard_count
     n_side = None

@@ -236,6 +236,7 @@ sbc_batch *batch_create(const sbc_graph *const *gs_in, size_t n, int p, int q, b
         spec.l = (p == q || sd == 0) ? q : p;
         spec.pos_unit = pos_node_cost_setting();
         apply_tune(spec, tune);
+        spec.check = debug_checks_env();
         spec.per_graph = bg->totals.ptr;
         spec.graph_x0 = bg->x0.ptr;
         spec.n_graphs = (int)bg->members.size();
@@ -346,7 +347,7 @@ void autotune(const sbc_graph *const *gs, size_t n, int p, int q, int reps, sbc_
     sbc_tune_t cur{0, 0, 0, 0.0f};
     cur.ms = measure(cur);
     const int splits[] = {1, 2, 4, 8, 16};
-    const int smalls[] = {16, 32, 48, 64};
+    const int smalls[] = {32, 64, 128, 256, 512};
     const int costs[] = {2, 4, 6, 10, 16, 64, 1 << 20};
     auto sweep = [&](int32_t sbc_tune_t::*field, const int *vals, int nv) {
         sbc_tune_t best = cur;
@@ -359,7 +360,7 @@ void autotune(const sbc_graph *const *gs, size_t n, int p, int q, int reps, sbc_
         cur = best;
     };
     sweep(&sbc_tune_t::split_per_warp, splits, 5);
-    sweep(&sbc_tune_t::small_wedges, smalls, 4);
+    sweep(&sbc_tune_t::small_wedges, smalls, 5);
     sweep(&sbc_tune_t::pos_node_cost, costs, 7);
     *out = cur;
 }

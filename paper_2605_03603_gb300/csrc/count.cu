@@ -67,9 +67,10 @@ struct Counters {
 };
 
 enum : unsigned {
-    CERR_OVERFLOW = 1u,   // a binomial or the sum left 128 bits
+    CERR_OVERFLOW = kErrOverflow,  // a binomial or the sum left 128 bits
     CERR_RESERVE = 2u,    // candidate reservation exceeded (cannot happen)
     CERR_HASH = 4u,       // 2-hop table overflow after all retries
+    CERR_MASK = 8u,       // self-check: a candidate mask disagrees with its 2-hop counters
 };
 
 // Thresholds: the largest x for which binom(x, l) is computed exactly in 64
@@ -145,7 +146,7 @@ __device__ __noinline__ U128 binom_slow(unsigned long long x, int l, unsigned *e
 __device__ __forceinline__ void binom_add(U128 &acc, unsigned x, int l, unsigned *err) {
     if ((int)x < l) return;
     if (x > c_binom64_max[l]) {
-        acc.add(binom_slow(x, l, err));
+        if (acc.add(binom_slow(x, l, err))) atomicOr(err, CERR_OVERFLOW);
         return;
     }
     unsigned long long v;
@@ -238,7 +239,8 @@ __global__ void k_plan(const int64_t *__restrict__ A_off, const uint32_t *__rest
 //   bits  0..20  cnt over all positions (Algorithm 2's cnt[w])
 //   bits 21..41  cnt over useful positions (|P_w|)
 //   bits 42..62  useful positions with sign(u,v) != sign(w,v) (|D_w|)
-//   bit  63      set once w is kept; the low 32 bits then hold its index
+//   bit  63      set once w is kept; bits 0..20 then hold its candidate index
+//                (the other two counters stay, for the mask self-check)
 constexpr unsigned long long F_ALL = 1ull, F_USE = 1ull << 21, F_DIFF = 1ull << 42;
 constexpr unsigned long long M21 = (1ull << 21) - 1;
 constexpr unsigned long long CAND = 1ull << 63;
@@ -300,6 +302,28 @@ __device__ __forceinline__ unsigned long long pass1_add(uint32_t sdiff, uint32_t
     return bit != EMPTY ? (F_ALL | F_USE | (sdiff ? F_DIFF : 0ull)) : F_ALL;
 }
 
+// Kept candidate: index `c` in bits 0..20, the two useful-position counters
+// kept, CAND set.
+__device__ __forceinline__ unsigned long long cand_value(unsigned long long v, uint32_t c) {
+    return CAND | (v & ~(CAND | M21)) | (unsigned long long)c;
+}
+__device__ __forceinline__ uint32_t cand_index(unsigned long long v) { return (uint32_t)(v & M21); }
+
+// Self-check of one kept candidate after its masks are written: popc(P_w)
+// must equal its useful common neighbours and popc(D_w) its different-sign
+// ones (both counted by the hash table in the first pass). `P` and `D` are
+// the candidate's first words; consecutive words are `stride` apart. Reads
+// bypass L1 (the words were written by atomics at L2).
+__device__ __forceinline__ bool masks_match(const uint32_t *P, const uint32_t *D, size_t stride,
+                                            uint32_t W, unsigned long long v, bool global) {
+    uint32_t np = 0, nd = 0;
+    for (uint32_t w = 0; w < W; w++) {
+        np += __popc(global ? __ldcg(P + w * stride) : P[w * stride]);
+        nd += __popc(global ? __ldcg(D + w * stride) : D[w * stride]);
+    }
+    return np == (uint32_t)((v >> 21) & M21) && nd == (uint32_t)((v >> 42) & M21);
+}
+
 struct TwohopArgs {
     const int64_t *A_off;
     const uint32_t *A_ent, *A_pos, *A_bit;
@@ -318,19 +342,23 @@ struct TwohopArgs {
     unsigned large_begin, large_end;  // order[] ranges of the two kernels
     unsigned small_begin, small_end;
     int l;
+    int check;                      // run the candidate-mask self-check
+    uint32_t hs_cap;                // test override: most hash slots per table (0: none)
 };
+
+// Table size after the test override (which makes tables overflow on purpose,
+// to drive the CERR_HASH path).
+__device__ __forceinline__ uint32_t cap_slots(uint32_t hs, const TwohopArgs &a) {
+    return (a.hs_cap && hs > a.hs_cap) ? a.hs_cap : hs;
+}
 
 // ---- small anchors: one warp per anchor, private table in shared memory
 
 constexpr int PS_THREADS = 256;
 constexpr int PS_WARPS = PS_THREADS / 32;
 constexpr int PS_HS = 1024;            // slots per warp
-constexpr int SMALL_E = PS_HS / 2;     // visited wedges of a small anchor (load <= 1/2)
-// Default and largest tier threshold. Anchors of 256-512 visited wedges on
-// the warp tier lost candidate-mask bits on some graphs of the 10,000-graph
-// batch recipe (the CTA tier counts them exactly); until the cause is found
-// the warp tier takes anchors of at most 64 wedges.
-constexpr int SMALL_E_MAX = 64;
+// Default and largest tier threshold in visited wedges (table load <= 1/2).
+constexpr int SMALL_E_MAX = PS_HS / 2;
 constexpr size_t PS_SMEM = (size_t)PS_WARPS * PS_HS * 12;
 
 // Visit the anchor's 2-hop entries with one warp. fn(w, sdiff, bit).
@@ -408,6 +436,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_twohop_small(TwohopArgs a) {
         const unsigned long long e_vis = STATS ? a.e_all[r] : a.e_use[r];
         uint32_t hs = (uint32_t)(2 * e_vis + 31) & ~31u;
         hs = hs < 64 ? 64 : (hs > PS_HS ? PS_HS : hs);
+        hs = cap_slots(hs, a);
         for (uint32_t i = lane; i < hs; i += 32) {
             keys[i] = EMPTY;
             vals[i] = 0;
@@ -433,7 +462,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_twohop_small(TwohopArgs a) {
                     cand = keep_candidate(v, l);
                 }
                 uint32_t bal = __ballot_sync(FULL, cand);
-                if (cand) vals[i] = CAND | (ncw + __popc(bal & lt));
+                if (cand) vals[i] = cand_value(v, ncw + __popc(bal & lt));
                 ncw += __popc(bal);
                 npaper += __popc(__ballot_sync(FULL, pap));
             }
@@ -443,27 +472,34 @@ __global__ void __launch_bounds__(PS_THREADS) k_twohop_small(TwohopArgs a) {
                 ncw = 0;
             }
             if (ncw > 0) {
-                for (uint32_t i = lane; i < 2 * W * ncw; i += 32) {
-                    uint32_t wd = i / ncw, c = i % ncw;
-                    region[(size_t)wd * rsv + c] = 0;
-                }
-                // the zeroing stores of one lane must reach memory before other
-                // lanes' atomicOr on the same words (a warp barrier alone does
-                // not order plain stores against device-scope atomics)
-                __threadfence();
-                __syncwarp();
+                // The pool is zeroed on the stream before the 2-hop launches,
+                // so the masks are built by atomicOr alone (no zeroing stores
+                // of this kernel ever meet its atomics on the same words).
                 visit_warp(ebase, d, true, a.A_ent, a.A_pos, a.A_bit, a.B_off, a.B_ent,
                            [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
                                int sl = tab_find(keys, hs, w);
                                if (sl < 0) return;
                                unsigned long long v = vals[sl];
                                if (!(v & CAND)) return;
-                               uint32_t c = (uint32_t)v;
+                               uint32_t c = cand_index(v);
                                uint32_t m = 1u << (bit & 31);
                                size_t wd = bit >> 5;
                                atomicOr(&region[wd * rsv + c], m);
                                if (sdiff) atomicOr(&region[(W + wd) * rsv + c], m);
                            });
+                if (a.check) {
+                    __syncwarp();
+                    bool bad = false;
+                    for (uint32_t i = lane; i < hs; i += 32) {
+                        if (keys[i] == EMPTY) continue;
+                        unsigned long long v = vals[i];
+                        if (!(v & CAND)) continue;
+                        uint32_t c = cand_index(v);
+                        if (!masks_match(region + c, region + (size_t)W * rsv + c, rsv, W, v, true))
+                            bad = true;
+                    }
+                    if (__any_sync(FULL, bad) && lane == 0) atomicOr(&a.cnt->err, CERR_MASK);
+                }
             }
         }
         if (lane == 0) {
@@ -636,7 +672,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
             if (lane == 0 && bal) wbase = atomicAdd(&s_ncw, (unsigned)__popc(bal));
             if (lane == 0 && pb) atomicAdd(&s_paper, (unsigned)__popc(pb));
             wbase = __shfl_sync(FULL, wbase, 0);
-            if (cand) vals[i] = CAND | (wbase + __popc(bal & ((1u << lane) - 1u)));
+            if (cand) vals[i] = cand_value(vals[i], wbase + __popc(bal & ((1u << lane) - 1u)));
         }
     };
     auto set_bits = [&](uint32_t hs, uint32_t *bb, uint32_t bstride, uint32_t W, uint32_t w,
@@ -645,7 +681,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
         if (sl < 0) return;
         unsigned long long v = vals[sl];
         if (!(v & CAND)) return;
-        uint32_t c = (uint32_t)v;
+        uint32_t c = cand_index(v);
         uint32_t m = 1u << (bit & 31);
         size_t wd = bit >> 5;
         atomicOr(&bb[wd * bstride + c], m);
@@ -689,10 +725,22 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
                     uint32_t wd = i / ncw, c = i % ncw;
                     bb[(size_t)wd * bstride + c] = 0;
                 }
-                if (!staged) __threadfence();  // zeroing before other threads' atomicOr
                 __syncthreads();
                 pass2(bb, bstride);
                 __syncthreads();
+                if (a.check) {
+                    bool bad = false;
+                    for (uint32_t i = tid; i < hs; i += PL_THREADS) {
+                        if (keys[i] == EMPTY) continue;
+                        const unsigned long long v = vals[i];
+                        if (!(v & CAND)) continue;
+                        const uint32_t c = cand_index(v);
+                        if (!masks_match(bb + c, bb + (size_t)W * bstride + c, bstride, W, v, !staged))
+                            bad = true;
+                    }
+                    if (bad) atomicOr(&a.cnt->err, CERR_MASK);
+                    __syncthreads();
+                }
                 if (staged) {
                     for (uint32_t i = tid; i < 2 * W * ncw; i += PL_THREADS) {
                         uint32_t wd = i / ncw, c = i % ncw;
@@ -723,6 +771,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
             // one window
             uint32_t hs = (uint32_t)((2 * e_vis + 31) & ~31ull);
             hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
+            hs = cap_slots(hs, a);
             clear_table(hs);
             visit_block(ebase, d, !STATS, 0, 0, a, pst, ppre, pinfo, warp_tot, &s_total,
                         [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
@@ -768,6 +817,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
                     const unsigned long long *bk = bucket + (size_t)c * cap;
                     uint32_t hs = (uint32_t)((2ull * n + 31) & ~31ull);
                     hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
+                    hs = cap_slots(hs, a);
                     __syncthreads();
                     clear_table(hs);
                     for (uint32_t i = tid; i < n; i += PL_THREADS) {
@@ -807,6 +857,7 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
                 const unsigned long long per = (e_vis + nw - 1) >> lg_nw;
                 uint32_t hs = (uint32_t)((2 * per + 31) & ~31ull);
                 hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
+                hs = cap_slots(hs, a);
                 nc = 0;
                 npaper = 0;
                 bool restart = false;
@@ -1015,8 +1066,8 @@ __global__ void k_anchor_cost(ItemArgs a) {
             cost = (cost + c < cost) ? 0xFFFFFFFFFFFFFFFFull : cost + c;
         }
     }
-    tp = warp_sum_u128(tp);
-    to = warp_sum_u128(to);
+    tp = warp_sum_u128(tp, nullptr);
+    to = warp_sum_u128(to, nullptr);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         cand += __shfl_xor_sync(FULL, cand, o);
@@ -1024,8 +1075,8 @@ __global__ void k_anchor_cost(ItemArgs a) {
         cost = (cost + t < cost) ? 0xFFFFFFFFFFFFFFFFull : cost + t;
     }
     if ((threadIdx.x & 31) == 0) {
-        atomic_add_u128(a.cnt->tuples_paper, tp.lo, tp.hi);
-        atomic_add_u128(a.cnt->tuples_ours, to.lo, to.hi);
+        atomic_add_u128(a.cnt->tuples_paper, tp.lo, tp.hi, nullptr);
+        atomic_add_u128(a.cnt->tuples_ours, to.lo, to.hi, nullptr);
         atomicAdd(&a.cnt->candidates, cand);
         atomicAdd(&a.cnt->cost_total, cost);
     }
@@ -1908,7 +1959,7 @@ __device__ __forceinline__ void binom_add_r(U128 &acc, unsigned long long x, uns
         acc.add(x);
     } else {
         if (x > c_binom64_max[R]) {
-            acc.add(binom_slow(x, R, err));
+            if (acc.add(binom_slow(x, R, err))) atomicOr(err, CERR_OVERFLOW);
             return;
         }
         acc.add(binom_u64<R>(x));
@@ -1977,7 +2028,7 @@ __device__ __noinline__ PosOut pos_scan(uint32_t dp, uint32_t wc, uint32_t wcp, 
                     X.m1[k] = w < wc ? (M.m1[k] & sm_dyn[(dp + qc) * wcp + w]) : 0u;
                 }
                 const PosOut c = pos_scan<R, WPL, LEV + 1>(dp, wc, wcp, X, qc + 1, qe2, l, err);
-                out.sum.add(c.sum);
+                if (out.sum.add(c.sum)) atomicOr(err, CERR_OVERFLOW);
                 out.tested += c.tested;
                 out.leaves += c.leaves;
             }
@@ -2007,7 +2058,7 @@ __device__ void pos_unit_scan(uint32_t dp, uint32_t wc, uint32_t wcp, uint32_t q
     const uint32_t qe = qs + 31 < qe2 ? qs + 31 : qe2;
     if (qs > qe) return;
     const PosOut o = pos_scan<R, WPL, 2>(dp, wc, wcp, M, qs, qe, l, err);
-    acc.sum.add(o.sum);
+    if (acc.sum.add(o.sum)) atomicOr(err, CERR_OVERFLOW);
     acc.tested += o.tested;
     acc.leaves += o.leaves;
     acc.words += 2ull * wc * o.tested;
@@ -2137,7 +2188,7 @@ __device__ __forceinline__ void block_units(const MasksG &m, const Item &it, int
             const uint32_t nrows = it.i1 - ib < (uint32_t)BLK_I ? it.i1 - ib : (uint32_t)BLK_I;
             o = block_r2(m, wsm, ib, nrows, u - s_rowpre[lo], l, err);
         }
-        acc.sum.add(o.sum);
+        if (acc.sum.add(o.sum)) atomicOr(err, CERR_OVERFLOW);
         acc.tested += o.tested;
         acc.leaves += o.viable;
         acc.words += (unsigned long long)(o.closes + o.viable) * m.W;
@@ -2332,17 +2383,18 @@ __global__ void __launch_bounds__(PB_THREADS, 2) k_tuples(TupleArgs a) {
             if (!blocked)
                 cand_units<R>(mg, it, scratch, a.wmax, a.l, acc, err, &s_unit, &s_total, s_rowpre);
         }
-        U128 ws = warp_sum_u128(acc.sum);
+        U128 ws = warp_sum_u128(acc.sum, err);
         if (lane == 0 && (ws.lo | ws.hi)) {
-            atomic_add_u128(a.cnt->total, ws.lo, ws.hi);
-            if (a.per_anchor) atomic_add_u128(a.per_anchor + 2 * (size_t)r, ws.lo, ws.hi);
+            // a batch's union total is not a count (its graphs' totals are)
+            atomic_add_u128(a.cnt->total, ws.lo, ws.hi, a.per_graph ? nullptr : err);
+            if (a.per_anchor) atomic_add_u128(a.per_anchor + 2 * (size_t)r, ws.lo, ws.hi, err);
             if (a.per_graph) {
                 int lo = 0, hi = a.n_graphs;  // largest g with graph_x0[g] <= r
                 while (hi - lo > 1) {
                     int mid = (lo + hi) >> 1;
                     if (a.graph_x0[mid] <= (int64_t)r) lo = mid; else hi = mid;
                 }
-                atomic_add_u128(a.per_graph + 2 * (size_t)lo, ws.lo, ws.hi);
+                atomic_add_u128(a.per_graph + 2 * (size_t)lo, ws.lo, ws.hi, err);
             }
         }
 #pragma unroll
@@ -2490,6 +2542,7 @@ struct CountRun {
         if (per.ptr) SBC_CUDA(cudaMemsetAsync(per.ptr, 0, per.bytes(), s));
         if (spec.per_graph) SBC_CUDA(cudaMemsetAsync(spec.per_graph, 0, 16 * (size_t)spec.n_graphs, s));
         if (groups.empty()) return;
+        zero_pool(0);
         launch_twohop((unsigned)groups[0].first, (unsigned)groups[0].second);
         if (gt > 0) launch_tuple_kernel();
     }
@@ -2533,6 +2586,13 @@ struct CountRun {
         return (int64_t)(fr / 4 / 4);
     }
 
+    // The 2-hop kernels build candidate masks with atomicOr into a pool that
+    // is zero on entry (the CTA kernel also clears what it stages or redoes).
+    void zero_pool(size_t grp) {
+        const int64_t words = cum[groups[grp].second] - cum[groups[grp].first];
+        if (words > 0) SBC_CUDA(cudaMemsetAsync(pool.ptr, 0, (size_t)words * 4, s));
+    }
+
     void launch_twohop(unsigned a, unsigned b) {
         ta.large_begin = a;
         ta.large_end = b < hc.n_big ? b : hc.n_big;
@@ -2571,6 +2631,7 @@ struct CountRun {
     }
 
     std::vector<std::pair<int64_t, int64_t>> groups;  // ranges of the sorted anchors
+    std::vector<int64_t> cum;  // pool words before each sorted anchor
     float ms_twohop = 0, ms_tuples = 0;
 
     // Plan (with host reads of sizes) and execute once. Anchors are taken in
@@ -2615,7 +2676,7 @@ struct CountRun {
         SBC_CUDA(cudaStreamSynchronize(s));
         const int64_t n_act = hc.n_active;
         // candidate-mask words in heavy-first order, prefix sums, groups
-        std::vector<int64_t> cum(n_act + 1, 0);
+        cum.assign(n_act + 1, 0);
         {
             DevBuf<int64_t> dcum(n_act + 1, s);
             k_gather_words<<<grid_for(n_act + 1, B), B, 0, s>>>(sval.ptr, pool_off.ptr, n_act, dcum.ptr);
@@ -2657,6 +2718,8 @@ struct CountRun {
         ta.npaper = spec.paper ? npaper.ptr : nullptr;
         ta.cnt = cnt.ptr;
         ta.l = l;
+        ta.check = spec.check ? 1 : 0;
+        ta.hs_cap = hash_slots_cap();
         ta.bucket = nullptr;
         ta.bucket_slot = 0;
         if (hc.n_big > 0) {
@@ -2707,8 +2770,8 @@ struct CountRun {
         ia.pos_unit = spec.pos_unit;
         ia.cnt = cnt.ptr;
         n_items = 0;
-        for (const auto &grp : groups) {
-            const int64_t a = grp.first, b = grp.second, na = b - a;
+        for (size_t gi = 0; gi < groups.size(); gi++) {
+            const int64_t a = groups[gi].first, b = groups[gi].second, na = b - a;
             // this group's pool offsets and fresh queue heads
             k_group_offsets<<<grid_for(na, B), B, 0, s>>>(sval.ptr, cum_dev.ptr, a, b, pool_off.ptr);
             SBC_LAUNCHED();
@@ -2717,6 +2780,7 @@ struct CountRun {
             SBC_CUDA(cudaMemsetAsync(&cnt.ptr->cost_total, 0, sizeof(unsigned long long), s));
             cudaEvent_t t0 = timing ? new_event(ev_twohop) : nullptr;
             cudaEvent_t t1 = timing ? new_event(ev_twohop) : nullptr;
+            zero_pool(gi);
             if (t0) SBC_CUDA(cudaEventRecord(t0, s));
             launch_twohop((unsigned)a, (unsigned)b);
             if (t1) SBC_CUDA(cudaEventRecord(t1, s));
@@ -2799,6 +2863,9 @@ struct CountRun {
         SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
         SBC_CUDA(cudaStreamSynchronize(s));
         if (hc.err & CERR_OVERFLOW) fail(SBC_E_OVERFLOW, "balanced biclique count exceeds 128 bits");
+        if (hc.err & CERR_MASK)
+            fail(SBC_E_CUDA, "self-check failed: a candidate mask disagrees with its 2-hop "
+                             "counters (flags 0x%x)", hc.err);
         if (hc.err & (CERR_RESERVE | CERR_HASH))
             fail(SBC_E_CUDA, "internal error in the 2-hop kernel (flags 0x%x)", hc.err);
         res.count.lo = hc.total[0];
@@ -2881,6 +2948,24 @@ void apply_tune(CountSpec &spec, const sbc_tune_t *t) {
     if (t->split_per_warp) spec.split_per_warp = t->split_per_warp;
 }
 
+// SBC_HASH_SLOTS_CAP (tests only): caps every 2-hop hash table at this many
+// slots (rounded down to a multiple of 32, at least 32) so that tables
+// overflow and the kernels' CERR_HASH report can be exercised.
+uint32_t hash_slots_cap() {
+    const char *e = getenv("SBC_HASH_SLOTS_CAP");
+    if (!e || !*e) return 0;
+    long long v = atoll(e);
+    if (v <= 0) return 0;
+    if (v > (1 << 20)) v = 1 << 20;
+    v &= ~31ll;
+    return (uint32_t)(v < 32 ? 32 : v);
+}
+
+bool debug_checks_env() {
+    const char *e = getenv("SBC_DEBUG");
+    return e && *e && *e != '0';
+}
+
 unsigned long long pos_node_cost_setting() {
     unsigned long long u = kPosNodeCost;
     if (const char *e = getenv("SBC_POS_NODE_COST")) {  // tuning override
@@ -2911,6 +2996,7 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     spec.pos_unit = pos_node_cost_setting();
     apply_tune(spec, opts ? opts->tune : nullptr);
     spec.per_anchor = opts && opts->per_anchor;
+    spec.check = (opts && (opts->flags & SBC_COUNT_CHECK)) || debug_checks_env();
     if (spec.nshard < 0 || (spec.nshard > 0 && (spec.shard < 0 || spec.shard >= spec.nshard)))
         fail(SBC_E_INVAL, "bad shard %d of %d", spec.shard, spec.nshard);
     const int64_t kernels0 = g_launches.load();

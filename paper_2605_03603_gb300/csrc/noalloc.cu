@@ -19,6 +19,13 @@
 // relies on being zero. Calls are serialised by a host mutex; two processes
 // (or another user of the same device memory) running calls that overlap on
 // the GPU would race on the array.
+//
+// Inside a call the array is handed out as a stack: a block freed while a
+// later block is still live stays reserved until the call returns (every
+// call starts again from an empty array). A call that fails after it has
+// launched kernels waits for its stream before it returns and releases the
+// lock, so no kernel of a failed call can still be writing the array when
+// the next call starts.
 #include <mutex>
 
 #include "sbc_internal.cuh"
@@ -46,6 +53,13 @@ void *scratch_address() {
     }
     return g_noalloc_ptr[dev];
 }
+
+// Waits for the call's stream when the call ends (on every path, errors
+// included), before the arena and the lock are released.
+struct StreamDrain {
+    cudaStream_t s;
+    ~StreamDrain() { (void)cudaStreamSynchronize(s); }
+};
 
 struct ArenaScope {
     sbc::Arena arena;
@@ -76,6 +90,7 @@ extern "C" sbc_status sbc_count_csr_noalloc(int64_t n_u, int64_t n_v, int64_t nn
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
         ArenaScope scope(scratch_address());
         cudaStream_t s = (cudaStream_t)stream;
+        StreamDrain drain{s};
         std::unique_ptr<sbc_graph> g(
             sbc::create_graph(n_u, n_v, nnz, row_offsets, cols, signs, flags, s));
         sbc_count_stats st;

@@ -193,6 +193,7 @@ struct CountSpec {
     unsigned long long *per_graph = nullptr;  // device, 2 words per graph (batches)
     const int64_t *graph_x0 = nullptr;        // device, first anchor rank per graph
     int n_graphs = 0;
+    bool check = false;     // device self-checks (SBC_COUNT_CHECK or SBC_DEBUG=1)
 };
 struct CountResult {
     sbc_u128 count{0, 0}, anchor_tuples{0, 0};
@@ -220,6 +221,10 @@ void batch_destroy(sbc_batch *b);
 bool countrun_replayable(const CountRun *r);
 void countrun_destroy(CountRun *r);
 unsigned long long pos_node_cost_setting();
+// SBC_DEBUG set (and not "0") in the environment: self-checks on every count.
+bool debug_checks_env();
+// SBC_HASH_SLOTS_CAP (tests only): the 2-hop tables' slot cap, 0 for none.
+uint32_t hash_slots_cap();
 // Applies launch parameters (NULL or zero fields: defaults) to a count spec;
 // SBC_E_INVAL when a field is out of range.
 void apply_tune(CountSpec &spec, const sbc_tune_t *t);
@@ -230,16 +235,36 @@ void apply_tune(CountSpec &spec, const sbc_tune_t *t);
 
 namespace sbc {
 
+// Error bit of a count whose exact value (or one of its terms) needs more
+// than 128 bits.
+constexpr unsigned kErrOverflow = 1u;
+
 // Add the unsigned 128-bit value (lo, hi) into *dst (two 64-bit words) with
-// 64-bit atomics: the limb add that wraps carries into the high word.
+// 64-bit atomics: the limb add that wraps carries into the high word. A carry
+// out of the high word (the sum left 128 bits) sets kErrOverflow in *err
+// (when err is not NULL).
 __device__ __forceinline__ void atomic_add_u128(unsigned long long *dst, unsigned long long lo,
-                                                unsigned long long hi) {
+                                                unsigned long long hi, unsigned *err) {
+    bool ovf = false;
     if (lo) {
         unsigned long long old = atomicAdd(dst, lo);
-        if (old + lo < old) hi += 1;
+        if (old + lo < old) {
+            hi += 1;
+            ovf = hi == 0;
+        }
     }
-    if (hi) atomicAdd(dst + 1, hi);
+    if (hi) {
+        unsigned long long old = atomicAdd(dst + 1, hi);
+        ovf |= old + hi < old;
+    }
+    if (ovf && err) atomicOr(err, kErrOverflow);
 }
+
+// A thread's partial sum is flagged once its high word passes this value:
+// from below it, the 64-bit adds a thread makes (far fewer than 2^48) cannot
+// carry the high word past 2^64, so the only wraps left to detect are the
+// 128-bit adds, which check exactly.
+constexpr unsigned long long kU128Headroom = 0xFFFF000000000000ull;
 
 struct U128 {
     unsigned long long lo = 0, hi = 0;
@@ -247,20 +272,30 @@ struct U128 {
         lo += v;
         hi += (lo < v) ? 1ull : 0ull;
     }
-    __device__ __forceinline__ void add(U128 v) {
+    // Returns true when the sum left 128 bits or passed the headroom mark.
+    __device__ __forceinline__ bool add(U128 v) {
         lo += v.lo;
-        hi += v.hi + ((lo < v.lo) ? 1ull : 0ull);
+        const unsigned long long c = lo < v.lo ? 1ull : 0ull;
+        const unsigned long long h = hi + v.hi;
+        bool o = h < hi;
+        hi = h + c;
+        o |= hi < h;
+        return o || hi > kU128Headroom;
     }
 };
 
-__device__ __forceinline__ U128 warp_sum_u128(U128 v) {
+// Sum of the warp's values (every lane gets it); sets kErrOverflow in *err
+// (when not NULL) if a partial sum leaves 128 bits.
+__device__ __forceinline__ U128 warp_sum_u128(U128 v, unsigned *err) {
+    bool o = false;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int k = 16; k > 0; k >>= 1) {
         U128 t;
-        t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-        t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
-        v.add(t);
+        t.lo = __shfl_xor_sync(0xffffffffu, v.lo, k);
+        t.hi = __shfl_xor_sync(0xffffffffu, v.hi, k);
+        o |= v.add(t);
     }
+    if (err && __any_sync(0xffffffffu, o) && (threadIdx.x & 31) == 0) atomicOr(err, kErrOverflow);
     return v;
 }
 

@@ -276,9 +276,9 @@ def tiny_random(seed: int, n_u: int, n_v: int, density: float, neg: float) -> Si
 
 
 def batch_graphs(seed: int, count: int, m_lo: float = 500, m_hi: float = 500_000,
-                 threads: int = 0):
-    """Graphs 0..count-1 of a batch, generated on host threads (the C sampler
-    releases the interpreter lock)."""
+                 threads: int = 0, start: int = 0):
+    """Graphs start..start+count-1 of a batch, generated on host threads (the
+    C sampler releases the interpreter lock)."""
     threads = threads or min(32, os.cpu_count() or 1)
     with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
-        return list(ex.map(lambda i: batch_graph(seed, i, m_lo, m_hi), range(count)))
+        return list(ex.map(lambda i: batch_graph(seed, i, m_lo, m_hi), range(start, start + count)))

@@ -91,7 +91,7 @@ def test_autotuner_choice_counts_exactly(sbc):
     try:
         t = sbc.sbc_autotune(hs, 3, 3, reps=2)
         assert t["split_per_warp"] in (0, 1, 2, 4, 8, 16)
-        assert t["small_wedges"] in (0, 16, 32, 48, 64)
+        assert t["small_wedges"] in (0, 32, 64, 128, 256, 512)
         assert t["pos_node_cost"] in (0, 2, 4, 6, 10, 16, 64, 1 << 20)
         assert t["ms"] > 0
         with sbc.Batch(hs, 3, 3, tune=t) as b:
@@ -107,7 +107,7 @@ def test_autotuner_choice_counts_exactly(sbc):
 
 
 @pytest.mark.parametrize("tune", [
-    {"small_wedges": 64, "pos_node_cost": 2, "split_per_warp": 16},
+    {"small_wedges": 512, "pos_node_cost": 2, "split_per_warp": 16},
     {"small_wedges": 32, "pos_node_cost": 1 << 20, "split_per_warp": 1},
     {"small_wedges": 1, "pos_node_cost": 1, "split_per_warp": 64},
 ])
@@ -123,7 +123,7 @@ def test_extreme_launch_parameters_exact(sbc, tune):
 def test_launch_parameters_out_of_range_rejected(sbc):
     g = sbc_synth.plain_small()
     with sbc.graph_from_synth(g) as h:
-        for bad in [{"small_wedges": 65}, {"split_per_warp": 65}, {"pos_node_cost": -1},
+        for bad in [{"small_wedges": 513}, {"split_per_warp": 65}, {"pos_node_cost": -1},
                     {"small_wedges": -2}]:
             with pytest.raises(sbc.SbcError) as e:
                 sbc.sbc_count_ex(h, 3, 3, tune=bad)
@@ -132,17 +132,28 @@ def test_launch_parameters_out_of_range_rejected(sbc):
         sbc.sbc_autotune([], 3, 3)
 
 
+def _side(sbc, h):
+    info = sbc.sbc_graph_info(h)
+    return 0 if info["wedges_anchor_u"] <= info["wedges_anchor_v"] else 1
+
+
 @pytest.mark.parametrize("index", [4829, 7100])
 def test_batch_recipe_graphs_exact(sbc, index):
     """Two graphs of the 10,000-graph batch recipe (about 2.4e5 and 4.9e5
-    edges) whose counts once came out a few bicliques short: alone, in a
-    small batch and with every 2-hop tier threshold, against the oracle."""
+    edges) whose counts once came out a few bicliques short on the
+    warp-per-anchor 2-hop tier: per anchor against the oracle with the tier
+    threshold forced to 1 (every anchor on the CTA tier), 64, 256 and 512
+    wedges, with the mask self-check on; alone and in a small batch."""
     g = sbc_synth.batch_graph(4, index)
-    want = oracle.count(g, 3, 3, side=0)
     with sbc.graph_from_synth(g) as h:
+        side = _side(sbc, h)
+        want, want_per = oracle.count(g, 3, 3, side=side, per_anchor=True)
         assert sbc.sbc_count(h, 3, 3) == want
-        for sw in (1, 16, 64):
-            assert sbc.sbc_count_ex(h, 3, 3, tune={"small_wedges": sw})[0] == want
+        for sw in (1, 64, 256, 512):
+            got, _, per = sbc.sbc_count_ex(h, 3, 3, anchor_side=side, per_anchor=True,
+                                            tune={"small_wedges": sw}, check=True)
+            assert got == want, sw
+            assert per == want_per, sw
         other = sbc.graph_from_synth(sbc_synth.batch_graph(4, index + 1))
         try:
             assert sbc.sbc_count_batch([h, other], 3, 3)[0] == want
@@ -150,21 +161,40 @@ def test_batch_recipe_graphs_exact(sbc, index):
             other.close()
 
 
-def test_two_hop_tiers_agree_on_batch_recipe(sbc):
-    """Per-graph counts of 300 graphs from the batch recipe's generator
-    (edges up to 2e5) are the same whichever 2-hop kernel takes the anchors
-    (CTA per anchor for all, or the warp kernel up to its 64-wedge cap),
-    alone and batched; small ones also against the oracle."""
-    gs = sbc_synth.batch_graphs(4, 300, 500, 200_000)
+def test_two_hop_tiers_per_anchor_on_batch_recipe(sbc):
+    """300 graphs from the batch recipe's generator (edges up to 5e4): per
+    anchor against the oracle with the warp tier threshold at 64, 256 and 512
+    wedges (self-check on), and batched."""
+    gs = sbc_synth.batch_graphs(4, 300, 500, 50_000)
     hs = [sbc.graph_from_synth(g) for g in gs]
     try:
-        cta = [sbc.sbc_count_ex(h, 3, 3, tune={"small_wedges": 1})[0] for h in hs]
-        warp = [sbc.sbc_count_ex(h, 3, 3, tune={"small_wedges": 64})[0] for h in hs]
-        assert warp == cta
-        assert sbc.sbc_count_batch(hs, 3, 3) == cta
-        for i in range(0, 300, 60):
-            if gs[i].m <= 20_000:
-                assert cta[i] == oracle.count(gs[i], 3, 3, side=0)
+        want = []
+        for g, h in zip(gs, hs):
+            side = _side(sbc, h)
+            c, per = oracle.count(g, 3, 3, side=side, per_anchor=True)
+            want.append(c)
+            for sw in (64, 256, 512):
+                got, _, gp = sbc.sbc_count_ex(h, 3, 3, anchor_side=side, per_anchor=True,
+                                               tune={"small_wedges": sw}, check=True)
+                assert got == c and gp == per, (g.name if hasattr(g, "name") else None, sw)
+        assert sbc.sbc_count_batch(hs, 3, 3) == want
     finally:
         for h in hs:
             h.close()
+
+
+def test_batch_recipe_all_graphs_plain_equals_batched(sbc):
+    """All 10,000 graphs of the batch recipe (7.2e8 edges, in chunks of 1,000):
+    plain per-graph counts with the warp tier at its 512-wedge default and the
+    mask self-check on equal the batched counts of each chunk. This is the
+    workload on which the warp tier once lost candidate-mask bits."""
+    for c0 in range(0, 10_000, 1000):
+        gs = sbc_synth.batch_graphs(4, 1000, start=c0)
+        hs = [sbc.graph_from_synth(g) for g in gs]
+        del gs
+        try:
+            plain = [sbc.sbc_count_ex(h, 3, 3, check=True)[0] for h in hs]
+            assert sbc.sbc_count_batch(hs, 3, 3) == plain, c0
+        finally:
+            for h in hs:
+                h.close()
