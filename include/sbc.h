@@ -142,12 +142,20 @@ sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
  *   split_per_warp work items per warp of a full-GPU tuple launch: heavy
  *                  anchors are split into items of about (estimated total
  *                  cost) / (resident warps x split_per_warp). 1..64, default 4.
+ *   tc_min_words   anchors with two partners (tuple size 3 on the anchor side)
+ *                  whose candidate masks have at least this many 32-bit words
+ *                  (and at least 128 candidates) take the tensor-core pair
+ *                  step: the four type-class sizes of every candidate pair are
+ *                  entries of a Gram matrix of the candidates' 0/1 masks,
+ *                  computed by tcgen05 MMAs. -1 turns the step off, 1..65536
+ *                  sets the threshold, default 5.
  * SBC_E_INVAL for a field outside its range.
  */
 typedef struct {
     int32_t small_wedges;
     int32_t pos_node_cost;
     int32_t split_per_warp;
+    int32_t tc_min_words;
     float ms; /* sbc_autotune: time of one count with the chosen parameters */
 } sbc_tune_t;
 
@@ -186,6 +194,11 @@ typedef struct {
     float ms_twohop;        /* 2-hop candidate kernel */
     float ms_tuples;        /* tuple / type-count kernel */
     float ms_total;
+    float ms_tc;            /* tensor-core pair step (mask expansion + MMA kernel) */
+    uint64_t tc_anchors;    /* anchors whose pairs the tensor-core step counted */
+    uint64_t tc_tiles;      /* 128 x 256 Gram-matrix tiles it computed */
+    uint64_t tc_kblocks;    /* K steps of 128 positions over those tiles: the step made
+                               tc_kblocks x 128 x 256 x 128 multiply-adds */
 } sbc_count_stats;
 
 /*

@@ -64,11 +64,13 @@ class GraphInfo(ctypes.Structure):
 class Tune(ctypes.Structure):
     """sbc_tune_t: launch parameters of the counting kernels (0 = default)."""
     _fields_ = [("small_wedges", ctypes.c_int32), ("pos_node_cost", ctypes.c_int32),
-                ("split_per_warp", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("split_per_warp", ctypes.c_int32), ("tc_min_words", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {"small_wedges": int(self.small_wedges), "pos_node_cost": int(self.pos_node_cost),
-                "split_per_warp": int(self.split_per_warp), "ms": float(self.ms)}
+                "split_per_warp": int(self.split_per_warp), "tc_min_words": int(self.tc_min_words),
+                "ms": float(self.ms)}
 
 
 def _tune(t) -> "Tune | None":
@@ -77,7 +79,7 @@ def _tune(t) -> "Tune | None":
     if isinstance(t, Tune):
         return t
     return Tune(int(t.get("small_wedges", 0)), int(t.get("pos_node_cost", 0)),
-                int(t.get("split_per_warp", 0)), 0.0)
+                int(t.get("split_per_warp", 0)), int(t.get("tc_min_words", 0)), 0.0)
 
 
 class CountOpts(ctypes.Structure):
@@ -93,7 +95,9 @@ class CountStats(ctypes.Structure):
                 ("popc_words", ctypes.c_uint64),
                 ("anchor_side", ctypes.c_int32), ("kernels", ctypes.c_int32),
                 ("ms_prepare", ctypes.c_float), ("ms_twohop", ctypes.c_float),
-                ("ms_tuples", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_tuples", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("ms_tc", ctypes.c_float), ("tc_anchors", ctypes.c_uint64),
+                ("tc_tiles", ctypes.c_uint64), ("tc_kblocks", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {"count": self.count.value(), "anchor_tuples": self.anchor_tuples.value(),
@@ -103,7 +107,9 @@ class CountStats(ctypes.Structure):
                 "anchor_side": int(self.anchor_side),
                 "kernels": int(self.kernels), "ms_prepare": float(self.ms_prepare),
                 "ms_twohop": float(self.ms_twohop), "ms_tuples": float(self.ms_tuples),
-                "ms_total": float(self.ms_total)}
+                "ms_total": float(self.ms_total), "ms_tc": float(self.ms_tc),
+                "tc_anchors": int(self.tc_anchors), "tc_tiles": int(self.tc_tiles),
+                "tc_kblocks": int(self.tc_kblocks)}
 
 
 _vp = ctypes.c_void_p

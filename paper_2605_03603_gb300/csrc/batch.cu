@@ -344,7 +344,7 @@ void autotune(const sbc_graph *const *gs, size_t n, int p, int q, int reps, sbc_
                              "changed a count", t.small_wedges, t.pos_node_cost, t.split_per_warp);
         return best;
     };
-    sbc_tune_t cur{0, 0, 0, 0.0f};
+    sbc_tune_t cur{0, 0, 0, 0, 0.0f};
     cur.ms = measure(cur);
     const int splits[] = {1, 2, 4, 8, 16};
     const int smalls[] = {32, 64, 128, 256, 512};
@@ -362,6 +362,8 @@ void autotune(const sbc_graph *const *gs, size_t n, int p, int q, int reps, sbc_
     sweep(&sbc_tune_t::split_per_warp, splits, 5);
     sweep(&sbc_tune_t::small_wedges, smalls, 5);
     sweep(&sbc_tune_t::pos_node_cost, costs, 7);
+    const int tcs[] = {-1, 3, 5, 9, 17};
+    sweep(&sbc_tune_t::tc_min_words, tcs, 5);
     *out = cur;
 }
 

@@ -52,7 +52,7 @@ struct Counters {
     unsigned int n_active;             // anchors with work
     unsigned int n_big;                // anchors for the CTA-wide 2-hop kernel
     unsigned int n_items;
-    unsigned int plan_pad;
+    unsigned int n_tc;                 // anchors of the group for the tensor-core pair step
     // ---- per execution
     unsigned long long run_begin;      // marker (unused)
     unsigned long long total[2];       // u128 count
@@ -68,6 +68,7 @@ struct Counters {
 
 enum : unsigned {
     CERR_OVERFLOW = kErrOverflow,  // a binomial or the sum left 128 bits
+    CERR_TIMEOUT = kErrTimeout,    // a bounded wait of the tensor-core kernel ran out
     CERR_RESERVE = 2u,    // candidate reservation exceeded (cannot happen)
     CERR_HASH = 4u,       // 2-hop table overflow after all retries
     CERR_MASK = 8u,       // self-check: a candidate mask disagrees with its 2-hop counters
@@ -957,6 +958,10 @@ struct ItemArgs {
     Item *items;
     uint32_t *ikey, *ival;
     Counters *cnt;
+    // tensor-core pair step (two partners, candidate side, wide masks)
+    int tc_on;
+    uint32_t tc_min_w, tc_min_nc;
+    uint32_t *tc_list;
 };
 
 __device__ __forceinline__ unsigned long long row_cost(uint32_t nc, uint32_t i, int R, uint32_t W) {
@@ -1028,7 +1033,15 @@ __device__ __forceinline__ bool use_pos(uint32_t nc, uint32_t dp, int R, int l, 
     return pos_cost(nc, dp, l, unit) < cand_cost(nc, (dp + 31) / 32, R);
 }
 
-// Anchor cost, anchor tuple counts. Thread per anchor.
+// True when the anchor's pairs go to the tensor-core kernel (tc_pairs.cu):
+// two partners, candidate side, at least tc_min_w mask words and tc_min_nc
+// candidates.
+__device__ __forceinline__ bool tc_take(const ItemArgs &a, uint32_t nc, uint32_t dp) {
+    return a.tc_on && a.R == 2 && nc >= a.tc_min_nc && (dp + 31) / 32 >= a.tc_min_w &&
+           !use_pos(nc, dp, a.R, a.l, a.method, a.pos_unit);
+}
+
+// Anchor cost, anchor tuple counts, tensor-core anchor list. Thread per anchor.
 __global__ void k_anchor_cost(ItemArgs a) {
     U128 tp, to;
     unsigned long long cand = 0, cost = 0;
@@ -1061,9 +1074,14 @@ __global__ void k_anchor_cost(ItemArgs a) {
         if (nc >= (uint32_t)a.R) {
             unsigned long long t = binom_sat(nc, a.R);
             to.add(t);
-            unsigned long long c = use_pos(nc, a.dprime[r], a.R, a.l, a.method, a.pos_unit) ? pos_cost(nc, a.dprime[r], a.l, a.pos_unit)
-                                                                     : cand_cost(nc, W, a.R);
-            cost = (cost + c < cost) ? 0xFFFFFFFFFFFFFFFFull : cost + c;
+            if (tc_take(a, nc, a.dprime[r])) {
+                a.tc_list[atomicAdd(&a.cnt->n_tc, 1u)] = r;
+            } else {
+                unsigned long long c = use_pos(nc, a.dprime[r], a.R, a.l, a.method, a.pos_unit)
+                                           ? pos_cost(nc, a.dprime[r], a.l, a.pos_unit)
+                                           : cand_cost(nc, W, a.R);
+                cost = (cost + c < cost) ? 0xFFFFFFFFFFFFFFFFull : cost + c;
+            }
         }
     }
     tp = warp_sum_u128(tp, nullptr);
@@ -1109,7 +1127,9 @@ __global__ void k_items(ItemArgs a) {
             n++;
         };
         const uint32_t dp = a.dprime[r];
-        if (nc >= (uint32_t)R && nc > 0 && use_pos(nc, dp, R, a.l, a.method, a.pos_unit)) {
+        if (nc >= (uint32_t)R && nc > 0 && tc_take(a, nc, dp)) {
+            // the tensor-core kernel takes this anchor's pairs: no items
+        } else if (nc >= (uint32_t)R && nc > 0 && use_pos(nc, dp, R, a.l, a.method, a.pos_unit)) {
             const uint32_t rows = dp - a.l + 1;
             const unsigned long long cap = 4 * a.item_cost;
             uint32_t rb = 0;
@@ -1176,6 +1196,22 @@ __global__ void k_items(ItemArgs a) {
         if (!EMIT) a.item_cnt[ix] = n;
     }
     if (!EMIT && blockIdx.x == 0 && threadIdx.x == 0) a.item_cnt[a.nX] = 0;
+}
+
+// Inputs of the tensor-core plan: the listed anchors' sizes and pool offsets.
+__global__ void k_tc_gather(const uint32_t *list, unsigned n, const uint32_t *ncand,
+                            const uint32_t *dprime, const uint32_t *rsv_c, const int64_t *pool_off,
+                            TcInput *out) {
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t r = list[i];
+        TcInput t;
+        t.r = r;
+        t.nc = ncand[r];
+        t.W = (dprime[r] + 31) / 32;
+        t.rsv = rsv_c[r];
+        t.pool_off = pool_off[r];
+        out[i] = t;
+    }
 }
 
 // ------------------------------------------------------------------ tuples
@@ -2423,6 +2459,10 @@ namespace {
 constexpr unsigned long long kPosNodeCost = 3;
 // Default tuple work items per resident warp of a full launch.
 constexpr unsigned long long kSplitPerWarp = 4;
+// Two-partner anchors with at least this many mask words and candidates take
+// the tensor-core pair step.
+constexpr uint32_t kTcMinWords = 5;
+constexpr uint32_t kTcMinCandidates = 128;
 
 // Largest x with binom(x, l) computable in 64 bits by the multiplicative
 // formula: every partial product binom(x-l+i, i) * i must stay below 2^64.
@@ -2467,6 +2507,7 @@ void ensure_kernel_attrs() {
     SBC_CUDA(cudaFuncSetAttribute(k_twohop_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PS_SMEM));
     SBC_CUDA(cudaFuncSetAttribute(k_twohop_large<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL_SMEM));
     SBC_CUDA(cudaFuncSetAttribute(k_twohop_large<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL_SMEM));
+    tc_ensure_attrs();
     set_tuple_attr<1>();
     set_tuple_attr<2>();
     set_tuple_attr<3>();
@@ -2525,6 +2566,9 @@ struct CountRun {
     DevBuf<unsigned long long> e_use, e_all, bucket, per;
     DevBuf<int64_t> pool_off, dtot, item_off, cum_dev;
     DevBuf<Item> items;
+    DevBuf<uint32_t> tc_list;
+    DevBuf<unsigned char> zbuf;     // Z arena of the tensor-core pair step
+    std::vector<TcPlan> tc_plans;   // per anchor group
     TwohopArgs ta;
     TupleArgs tu;
     int ga = 0, gs = 0, gt = 0;
@@ -2545,6 +2589,32 @@ struct CountRun {
         zero_pool(0);
         launch_twohop((unsigned)groups[0].first, (unsigned)groups[0].second);
         if (gt > 0) launch_tuple_kernel();
+        launch_tc(0);
+    }
+
+    // Tensor-core pair step of group `grp` (expansion and pair kernels of each
+    // of its chunks).
+    void launch_tc(size_t grp) {
+        if (grp >= tc_plans.size() || tc_plans[grp].anchors == 0) return;
+        TcArgs ta2;
+        ta2.pool = pool.ptr;
+        ta2.l = spec.l;
+        ta2.total = cnt.ptr->total;
+        ta2.per_anchor = per.ptr;
+        ta2.per_graph = spec.per_graph;
+        ta2.graph_x0 = spec.graph_x0;
+        ta2.n_graphs = spec.n_graphs;
+        ta2.err = &cnt.ptr->err;
+        ta2.big64 = binom64_limit(spec.l);
+        tc_launch(tc_plans[grp], ta2, zbuf.ptr, s);
+    }
+
+    // Bytes of Z one tensor-core chunk may take.
+    int64_t tc_budget_bytes() const {
+        size_t fr = 0, tot = 0;
+        SBC_CUDA(cudaMemGetInfo(&fr, &tot));
+        int64_t b = (int64_t)(fr / 8);
+        return std::max<int64_t>(256ll << 20, std::min<int64_t>(b, 8ll << 30));
     }
 
     // Events around the 2-hop and tuple launches of each group (pairs).
@@ -2558,8 +2628,10 @@ struct CountRun {
     void drop_events() {
         for (cudaEvent_t e : ev_twohop) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_tuples) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_tc) cudaEventDestroy(e);
         ev_twohop.clear();
         ev_tuples.clear();
+        ev_tc.clear();
     }
     static float pairs_ms(const std::vector<cudaEvent_t> &v) {
         float sum = 0;
@@ -2632,16 +2704,48 @@ struct CountRun {
 
     std::vector<std::pair<int64_t, int64_t>> groups;  // ranges of the sorted anchors
     std::vector<int64_t> cum;  // pool words before each sorted anchor
-    float ms_twohop = 0, ms_tuples = 0;
+    float ms_twohop = 0, ms_tuples = 0, ms_tc = 0;
+    std::vector<cudaEvent_t> ev_tc;
 
     // Plan (with host reads of sizes) and execute once. Anchors are taken in
     // heavy-first order in groups whose candidate masks fit the pool budget;
     // each group runs its 2-hop kernels, item planning and tuple kernel.
+    // Tensor-core plan of group `grp` from the n anchors k_anchor_cost listed.
+    void plan_tc(size_t grp, unsigned n) {
+        DevBuf<TcInput> tin(n, s);
+        k_tc_gather<<<grid_for(n, 256), 256, 0, s>>>(tc_list.ptr, n, ncand.ptr, dprime.ptr,
+                                                    rsv_c.ptr, pool_off.ptr, tin.ptr);
+        SBC_LAUNCHED();
+        g_launches++;
+        std::vector<TcInput> h(n);
+        SBC_CUDA(cudaMemcpyAsync(h.data(), tin.ptr, sizeof(TcInput) * n, cudaMemcpyDeviceToHost, s));
+        SBC_CUDA(cudaStreamSynchronize(s));
+        TcPlan plan = tc_plan(h, tc_budget_bytes());
+        tc_upload(plan, s);
+        const size_t need = (size_t)plan.max_blocks * (size_t)kTcBlockBytes;
+        if (need > zbuf.bytes()) zbuf.alloc(need, s);
+        tc_anchors += (uint64_t)plan.anchors;
+        tc_tiles += (uint64_t)plan.tiles;
+        tc_kblocks += plan.kblocks;
+        tc_plans[grp] = std::move(plan);
+    }
+
+    void run_tc_timed(size_t grp, bool timing) {
+        if (grp >= tc_plans.size() || tc_plans[grp].anchors == 0) return;
+        cudaEvent_t t4 = timing ? new_event(ev_tc) : nullptr;
+        cudaEvent_t t5 = timing ? new_event(ev_tc) : nullptr;
+        if (t4) SBC_CUDA(cudaEventRecord(t4, s));
+        launch_tc(grp);
+        if (t5) SBC_CUDA(cudaEventRecord(t5, s));
+    }
+    uint64_t tc_anchors = 0, tc_tiles = 0, tc_kblocks = 0;
+
     void plan_and_run(EventTimer *tm) {
         const bool timing = tm != nullptr;
         const int B = 256;
         groups.clear();
         drop_events();
+        tc_anchors = tc_tiles = tc_kblocks = 0;
         ta.large_begin = ta.large_end = ta.small_begin = ta.small_end = 0;
         gt = 0;
         const int l = spec.l;
@@ -2769,6 +2873,16 @@ struct CountRun {
         ia.method = spec.method;
         ia.pos_unit = spec.pos_unit;
         ia.cnt = cnt.ptr;
+        ia.tc_on = spec.tc_min_w >= 0 && R == 2 && !thread_arena_active();
+        ia.tc_min_w = spec.tc_min_w > 0 ? (uint32_t)spec.tc_min_w : kTcMinWords;
+        ia.tc_min_nc = kTcMinCandidates;
+        if (ia.tc_on) {
+            tc_list.alloc(nX, s);
+            tc_ensure_attrs();
+        }
+        ia.tc_list = tc_list.ptr;
+        tc_plans.clear();
+        tc_plans.resize(groups.size());
         n_items = 0;
         for (size_t gi = 0; gi < groups.size(); gi++) {
             const int64_t a = groups[gi].first, b = groups[gi].second, na = b - a;
@@ -2778,6 +2892,7 @@ struct CountRun {
             g_launches++;
             SBC_CUDA(cudaMemsetAsync(&cnt.ptr->head_large, 0, 3 * sizeof(unsigned), s));
             SBC_CUDA(cudaMemsetAsync(&cnt.ptr->cost_total, 0, sizeof(unsigned long long), s));
+            SBC_CUDA(cudaMemsetAsync(&cnt.ptr->n_tc, 0, sizeof(unsigned), s));
             cudaEvent_t t0 = timing ? new_event(ev_twohop) : nullptr;
             cudaEvent_t t1 = timing ? new_event(ev_twohop) : nullptr;
             zero_pool(gi);
@@ -2797,6 +2912,7 @@ struct CountRun {
             g_launches++;
             SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
             SBC_CUDA(cudaStreamSynchronize(s));
+            if (hc.n_tc > 0) plan_tc(gi, hc.n_tc);
             const unsigned long long spw =
                 spec.split_per_warp > 0 ? (unsigned long long)spec.split_per_warp : kSplitPerWarp;
             unsigned long long ic = hc.cost_total / ((unsigned long long)gb * PB_WARPS * spw);
@@ -2815,7 +2931,10 @@ struct CountRun {
                 SBC_CUDA(cudaStreamSynchronize(s));
             }
             if (ng > 0xFFFFFFF0ll) fail(SBC_E_UNSUPPORTED, "too many work items");
-            if (ng == 0) continue;
+            if (ng == 0) {
+                run_tc_timed(gi, timing);
+                continue;
+            }
             items.alloc(ng, s);
             ikey.alloc(ng, s);
             ival.alloc(ng, s);
@@ -2840,6 +2959,7 @@ struct CountRun {
             if (t2) SBC_CUDA(cudaEventRecord(t2, s));
             launch_tuple_kernel();
             if (t3) SBC_CUDA(cudaEventRecord(t3, s));
+            run_tc_timed(gi, timing);
             n_items += ng;
         }
         if (tm) tm->mark(4, s);
@@ -2847,6 +2967,7 @@ struct CountRun {
         if (timing) {
             ms_twohop = pairs_ms(ev_twohop);
             ms_tuples = pairs_ms(ev_tuples);
+            ms_tc = pairs_ms(ev_tc);
         }
         // planning scratch a replay does not need
         skey.release();
@@ -2866,6 +2987,9 @@ struct CountRun {
         if (hc.err & CERR_MASK)
             fail(SBC_E_CUDA, "self-check failed: a candidate mask disagrees with its 2-hop "
                              "counters (flags 0x%x)", hc.err);
+        if (hc.err & CERR_TIMEOUT)
+            fail(SBC_E_TIMEOUT, "a bounded wait of the tensor-core pair kernel ran out (flags 0x%x)",
+                 hc.err);
         if (hc.err & (CERR_RESERVE | CERR_HASH))
             fail(SBC_E_CUDA, "internal error in the 2-hop kernel (flags 0x%x)", hc.err);
         res.count.lo = hc.total[0];
@@ -2879,6 +3003,9 @@ struct CountRun {
         res.tested = hc.tested;
         res.typed = hc.leaves;
         res.popc_words = hc.popc_words;
+        res.tc_anchors = tc_anchors;
+        res.tc_tiles = tc_tiles;
+        res.tc_kblocks = tc_kblocks;
     }
 };
 
@@ -2943,9 +3070,12 @@ void apply_tune(CountSpec &spec, const sbc_tune_t *t) {
         fail(SBC_E_INVAL, "pos_node_cost must be in [0, 2^20], got %d", t->pos_node_cost);
     if (t->split_per_warp < 0 || t->split_per_warp > 64)
         fail(SBC_E_INVAL, "split_per_warp must be in [0, 64], got %d", t->split_per_warp);
+    if (t->tc_min_words < -1 || t->tc_min_words > 65536)
+        fail(SBC_E_INVAL, "tc_min_words must be in [-1, 65536], got %d", t->tc_min_words);
     if (t->small_wedges) spec.small_e = t->small_wedges;
     if (t->pos_node_cost) spec.pos_unit = (unsigned long long)t->pos_node_cost;
     if (t->split_per_warp) spec.split_per_warp = t->split_per_warp;
+    if (t->tc_min_words) spec.tc_min_w = t->tc_min_words;
 }
 
 // SBC_HASH_SLOTS_CAP (tests only): caps every 2-hop hash table at this many
@@ -3036,12 +3166,16 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
         stats->tuples_tested = res.tested;
         stats->tuples_typed = res.typed;
         stats->popc_words = res.popc_words;
+        stats->tc_anchors = res.tc_anchors;
+        stats->tc_tiles = res.tc_tiles;
+        stats->tc_kblocks = res.tc_kblocks;
         stats->kernels = (int32_t)(g_launches.load() - kernels0);
         if (tm.on) {
             stats->ms_total = tm.ms(0, 4);
             stats->ms_twohop = run->ms_twohop;
             stats->ms_tuples = run->ms_tuples;
-            stats->ms_prepare = stats->ms_total - run->ms_twohop - run->ms_tuples;
+            stats->ms_tc = run->ms_tc;
+            stats->ms_prepare = stats->ms_total - run->ms_twohop - run->ms_tuples - run->ms_tc;
         }
     }
 }

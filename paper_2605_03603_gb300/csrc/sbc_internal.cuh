@@ -11,6 +11,7 @@
 #include <atomic>
 #include <mutex>
 #include <memory>
+#include <vector>
 #include <stdexcept>
 #include <string>
 
@@ -194,10 +195,12 @@ struct CountSpec {
     const int64_t *graph_x0 = nullptr;        // device, first anchor rank per graph
     int n_graphs = 0;
     bool check = false;     // device self-checks (SBC_COUNT_CHECK or SBC_DEBUG=1)
+    int tc_min_w = 0;       // tensor-core pair step from this many mask words (0: default, -1: off)
 };
 struct CountResult {
     sbc_u128 count{0, 0}, anchor_tuples{0, 0};
     uint64_t candidates = 0, wedges = 0, work_items = 0, tested = 0, typed = 0, popc_words = 0;
+    uint64_t tc_anchors = 0, tc_tiles = 0, tc_kblocks = 0;
 };
 struct CountRun;
 struct EventTimer;
@@ -229,6 +232,54 @@ uint32_t hash_slots_cap();
 // SBC_E_INVAL when a field is out of range.
 void apply_tune(CountSpec &spec, const sbc_tune_t *t);
 
+// ---------------------------------------------------------------- tensor-core pairs
+
+// Tensor-core form of the two-partner tuple step for wide anchors
+// (tc_pairs.cu). One anchor of a chunk:
+struct TcAnchor {
+    uint32_t r;          // anchor rank
+    uint32_t nc, W, rsv; // candidates, mask words, candidate stride of its pool region
+    uint32_t RB, KB;     // Z row blocks of 128 (even), position blocks of 128
+    int64_t pool_off;    // its pool region (words)
+    int64_t zblk0;       // first Z block (16 KB each) in the chunk's arena
+    int64_t tile0;       // first output tile in the chunk
+};
+struct TcInput {
+    uint32_t r, nc, W, rsv;
+    int64_t pool_off;
+};
+struct TcChunk {
+    std::vector<TcAnchor> host;
+    DevBuf<TcAnchor> dev;
+    int64_t n_blocks = 0, n_tiles = 0;
+};
+struct TcPlan {
+    std::vector<TcChunk> chunks;
+    int64_t max_blocks = 0, tiles = 0, anchors = 0;
+    uint64_t kblocks = 0;  // sum over tiles of the anchor's position blocks (MMA K steps of 128)
+};
+struct TcArgs {
+    const TcAnchor *anc = nullptr;
+    int n_anc = 0;
+    int64_t n_blocks = 0, n_tiles = 0;
+    const uint32_t *pool = nullptr;
+    unsigned char *z = nullptr;
+    int l = 0;
+    unsigned long long *total = nullptr, *per_anchor = nullptr, *per_graph = nullptr;
+    const int64_t *graph_x0 = nullptr;
+    int n_graphs = 0;
+    unsigned *err = nullptr;
+    unsigned long long big64 = 0;  // largest x with binom(x, l) by the 64-bit formula
+};
+// Chunks of at most budget_bytes of Z (an anchor larger than that forms a
+// chunk of its own).
+TcPlan tc_plan(const std::vector<TcInput> &in, int64_t budget_bytes);
+void tc_upload(TcPlan &plan, cudaStream_t s);
+void tc_ensure_attrs();
+// Expansion + pair kernels of every chunk, in stream order (no host sync).
+void tc_launch(const TcPlan &plan, TcArgs base, unsigned char *z, cudaStream_t s);
+constexpr int64_t kTcBlockBytes = 16384;
+
 }  // namespace sbc
 
 // ---------------------------------------------------------------- device helpers
@@ -238,6 +289,8 @@ namespace sbc {
 // Error bit of a count whose exact value (or one of its terms) needs more
 // than 128 bits.
 constexpr unsigned kErrOverflow = 1u;
+// Error bit of a bounded device wait that ran out (the kernel stopped early).
+constexpr unsigned kErrTimeout = 16u;
 
 // Add the unsigned 128-bit value (lo, hi) into *dst (two 64-bit words) with
 // 64-bit atomics: the limb add that wraps carries into the high word. A carry

@@ -93,6 +93,7 @@ def test_autotuner_choice_counts_exactly(sbc):
         assert t["split_per_warp"] in (0, 1, 2, 4, 8, 16)
         assert t["small_wedges"] in (0, 32, 64, 128, 256, 512)
         assert t["pos_node_cost"] in (0, 2, 4, 6, 10, 16, 64, 1 << 20)
+        assert t["tc_min_words"] in (0, -1, 3, 5, 9, 17)
         assert t["ms"] > 0
         with sbc.Batch(hs, 3, 3, tune=t) as b:
             assert b.run() == want
