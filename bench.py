@@ -1,29 +1,37 @@
 #!/usr/bin/env python
-"""Benchmark: balanced (p,q)-biclique counting on one GB300 (or N, sharded).
+"""Benchmark: balanced (p,q)-biclique counting on one GB300 (or N replicas).
 
-Workload (default): one seeded signed Chung-Lu graph, |U| = 200,000,
-|V| = 100,000, 2,000,000 edges (exponents 2.0 on U, 2.3 on V, two planted
-factions with about 75% positive edges, flip probability 0.15), counted for
-(p,q) = (3,3) and (4,4).
+Workload (default): one seeded signed Chung-Lu graph, |U| = 5,000,000,
+|V| = 1,000,000, 60,000,000 edges (exponent 2.4 on U, 1.9 on V with V hubs
+capped at 50,000 expected degree, 4 planted factions with flip probability
+0.2), counted for (p,q) = (3,3). Inputs (the 60M-edge CSR, ~1.1 GB on the
+device) are larger than L2; L2 is also flushed between steps (512 MiB write).
 
 A step is the whole hot path on device-resident CSR input: graph build
-(validation, degrees, vertex priority, oriented adjacency) + the (3,3) count +
-the (4,4) count. The metric is anchor tuples per second: the number of
-(k-1)-subsets of candidates Algorithm 2 enumerates (sum over anchors of
-binom(|C(u)|, k-1), counted exactly once, outside the timed region), over the
-step time. Between timed steps L2 is flushed by writing a 512 MiB buffer.
+(validation, degrees, vertex priority, oriented adjacency) + the exact (3,3)
+count. The metric is anchor tuples per second: the number of (k-1)-subsets of
+candidates Algorithm 2 enumerates (sum over anchors of binom(|C(u)|, k-1),
+counted once, outside the timed region) over the step time; the line also
+gives seconds to the exact (3,3) count (seconds_to_exact_33).
 
-The line also carries: the tuple kernel's roofline (population counts per
-second against SMs x 16 per clock x the sampled SM clock, with its DRAM bytes
-per launch from an ncu capture), the 2-hop kernels' bytes per second, an
-end-to-end figure through the public API from pinned host buffers, the oracle
-timed on the host's cores on an anchor sample, a batch leg (graphs/s of the
-per-graph path, one batched count, a CUDA-graph replay and a replay with
-autotuned launch parameters) and a serving leg (p50/p99 and throughput under
-Poisson arrivals against one-at-a-time serving of the same arrivals).
+The line also carries:
+* roofline: the step's dominant kernel against its bound (the tuple kernel
+  in population counts per second against the POPC rate measured on this GPU
+  in the same run; the tensor-core pair kernel in fp8 TFLOP/s against the
+  measured bf16 peak times 2; the 2-hop kernels in bytes per second against
+  the measured HBM copy peak), and roofline_kernels with all three;
+* e2e: the same metric through the public API from pinned host buffers
+  (upload + build + count + the 16-byte result read);
+* cpu_baseline: the oracle (plain C, all host cores) on a bounded random
+  sample of anchors of the same count, with its estimate for the whole count;
+* medium: the 2M-edge graph, (3,3) + (4,4) per step;
+* batch: the 10,000-graph batch recipe (graphs/s of the per-graph path, one
+  batched count, CUDA-graph replay, replay with autotuned launch parameters);
+* serve: Poisson requests on resident graphs (p50/p99, throughput) against
+  a one-request-at-a-time server (one lane, no fusing) on the same arrivals.
 
---impl reference runs the CPU oracle (Algorithm 2 in plain C, all host cores)
-on a bounded random sample of anchors of the (3,3) count of the same workload
+--impl reference runs the oracle on the same workload and count, one bounded
+random anchor sample per step (graph lists built once, outside the timing),
 and reports the same metric.
 
 Multi-GPU (torchrun): anchors are sharded by rank (anchor rank mod N) over a
@@ -47,13 +55,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "anchor tuples/sec and seconds to exact balanced (3,3) count; batched graphs/sec, p99"
-WORKLOAD = "plain-200k-100k-2M"
-PQ = [(3, 3), (4, 4)]
-POPC_PER_CLK_PER_SM = 16  # 32-bit population count throughput per SM per clock
-# DRAM bytes (read + write) per tuple-kernel launch, mean of the (3,3) and (4,4)
-# launches, from one ncu capture of the current kernel
-# (profiles/k_tuples_traffic_plain-200k-100k-2M.md); None where not captured.
-TUPLE_TRAFFIC = {"plain-200k-100k-2M": 264_800_128}
+WORKLOAD = "plain-5M-1M-60M"
+PQ = [(3, 3)]
+# DRAM bytes (read + write) per launch of a kernel on a workload, from one ncu
+# capture of the current kernels; None where not captured.
+TRAFFIC = {}
 
 
 def _dist():
@@ -120,10 +126,10 @@ WORKLOADS = {"plain-200k-100k-2M": "plain_medium", "plain-50k-25k-500k": "plain_
              "plain-2k-1.5k-20k": "plain_small", "plain-5M-1M-60M": "plain_large"}
 
 
-def load_workload():
+def load_workload(name=None):
     import sbc_synth
 
-    return getattr(sbc_synth, WORKLOADS[WORKLOAD])()
+    return getattr(sbc_synth, WORKLOADS[name or WORKLOAD])()
 
 
 def measured_peaks():
@@ -131,23 +137,32 @@ def measured_peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def anchor_side(g) -> int:
+    """The side the library's cost model anchors on: fewer 2-paths to visit,
+    sum over the other side of binom(degree, 2) (ties: U)."""
+    du = np.diff(g.offsets).astype(np.float64)
+    dv = np.bincount(g.cols, minlength=g.n_v).astype(np.float64)
+    wu = float((dv * (dv - 1) / 2).sum())  # anchoring on U visits wedges through V
+    wv = float((du * (du - 1) / 2).sum())
+    return 0 if wu <= wv else 1
 
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(g, p, q, frac, seed, threads=0):
-    """Oracle (Algorithm 2, C, OpenMP) on a seeded random anchor sample.
+def oracle_sample(prep, g, side, p, q, frac, seed, threads=0):
+    """The oracle on a seeded random sample of anchors (lists already built).
     Returns (tuples, seconds, anchors, threads)."""
     import oracle
 
-    side = 0  # the anchor side the cost model picks for this workload (U)
     rng = np.random.default_rng(seed)
     n_s = g.n_u if side == 0 else g.n_v
     anchors = np.nonzero(rng.random(n_s) < frac)[0]
     t0 = time.perf_counter()
-    _, tuples = oracle.count(g, p, q, side=side, threads=threads, with_tuples=True,
-                             anchors=anchors)
+    _, tuples = prep.count(p, q, threads=threads, with_tuples=True, anchors=anchors)
     dt = time.perf_counter() - t0
     return tuples, dt, len(anchors), oracle.max_threads() if threads == 0 else threads
 
@@ -160,24 +175,31 @@ def run_reference(args):
 
     oracle.build()
     g = load_workload()
+    side = anchor_side(g)
+    p, q = PQ[0]
     frac = args.ref_frac
-    for i in range(args.warmup):
-        oracle_sample(g, 3, 3, frac, 100 + i)
     tot_t, tot_tuples, cores, anchors = 0.0, 0, 0, 0
-    for i in range(args.steps):
-        tup, dt, na, cores = oracle_sample(g, 3, 3, frac, 1000 + i)
-        tot_t += dt
-        tot_tuples += tup
-        anchors += na
+    with oracle.Prepared(g, side) as prep:
+        for i in range(args.warmup):
+            oracle_sample(prep, g, side, p, q, frac / 4, 100 + i)
+        for i in range(args.steps):
+            tup, dt, na, cores = oracle_sample(prep, g, side, p, q, frac, 1000 + i)
+            tot_t += dt
+            tot_tuples += tup
+            anchors += na
     value = tot_tuples / tot_t
-    sample = (f"(3,3) on a seeded random {frac:.1%} sample of U anchors per step "
-              f"({anchors // max(args.steps, 1)} anchors), oracle = Algorithm 2 in C with OpenMP")
+    side_name = "U" if side == 0 else "V"
+    sample = (f"({p},{q}) on a seeded random {frac:.3%} sample of {side_name} anchors per step "
+              f"({anchors // max(args.steps, 1)} anchors), oracle in C with OpenMP, graph "
+              f"lists built once before the timed steps")
+    est_s = (tot_t / args.steps) / frac  # the sampled anchors' time scaled to all anchors
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "anchor tuples/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * tot_t / max(args.steps, 1), "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pq": "(3,3)", "sample": sample},
+        "config": {"workload": WORKLOAD, "pq": f"({p},{q})", "sample": sample},
+        "seconds_to_exact_33_estimate": est_s,
         "cpu_baseline": {"value": value, "unit": "anchor tuples/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "anchor tuples/s", "h2d_bytes_per_step": 0,
@@ -187,13 +209,52 @@ def run_reference(args):
     return 0
 
 
-# ------------------------------------------------------------------ batch / serve legs
+# ------------------------------------------------------------------ extra legs
+
+def medium_leg(sbc, torch, args):
+    """The 2M-edge graph: graph build + (3,3) + (4,4) per step (3 timed steps)."""
+    g = load_workload("plain-200k-100k-2M")
+    off = torch.from_numpy(g.offsets).cuda()
+    col = torch.from_numpy(g.cols).cuda()
+    sgn = torch.from_numpy(g.signs).cuda()
+    pqs = [(3, 3), (4, 4)]
+    tuples, counts = {}, {}
+    with sbc.sbc_graph_create(g.n_u, g.n_v, off, col, sgn) as h:
+        for p, q in pqs:
+            c, st, _ = sbc.sbc_count_ex(h, p, q, paper_tuples=True)
+            counts[(p, q)], tuples[(p, q)] = c, st["anchor_tuples"]
+
+    def step():
+        with sbc.sbc_graph_create(g.n_u, g.n_v, off, col, sgn) as h:
+            out = []
+            for p, q in pqs:
+                c, st, _ = sbc.sbc_count_ex(h, p, q)
+                assert c == counts[(p, q)]
+                out.append(st)
+            return out
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sts = [step() for _ in range(3)]
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0) / 3
+    ms33 = float(np.mean([s[0]["ms_total"] for s in sts]))
+    return {"workload": "plain-200k-100k-2M", "pq": "(3,3)+(4,4)", "ms_per_step": ms,
+            "anchor_tuples_per_s": sum(tuples.values()) / (ms / 1e3),
+            "ms_33": ms33, "anchor_tuples_per_s_33": tuples[(3, 3)] / (ms33 / 1e3),
+            "counts": {str(k): v for k, v in counts.items()},
+            "phase_ms": {f"({p},{q})": {k: sts[-1][i][k] for k in
+                                         ("ms_twohop", "ms_tuples", "ms_tc", "ms_prepare")}
+                         for i, (p, q) in enumerate(pqs)}}
+
 
 def batch_leg(sbc, torch, args):
-    """Graphs/s for B independent graphs (the 10,000-graph batch recipe,
-    first B graphs): plain one-count-per-graph path, one batched count
-    (sbc_count_batch), a planned batch replayed from a CUDA graph, and the same
-    replay with the autotuner's launch parameters (tuning time reported)."""
+    """Graphs/s for B independent graphs of the 10,000-graph batch recipe:
+    plain one-count-per-graph path, one batched count (sbc_count_batch), a
+    planned batch replayed from a CUDA graph, and the same replay with the
+    autotuner's launch parameters (tuning time reported)."""
     import sbc_synth
 
     t0 = time.perf_counter()
@@ -204,6 +265,7 @@ def batch_leg(sbc, torch, args):
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     edges = sum(g.m for g in gs)
+    del gs
     p, q = 3, 3
 
     def timed(fn, reps):
@@ -215,18 +277,18 @@ def batch_leg(sbc, torch, args):
         return res, (time.perf_counter() - t) / reps
 
     plain, t_plain = timed(lambda: [sbc.sbc_count(h, p, q) for h in hs], 1)
-    batched, t_batch = timed(lambda: sbc.sbc_count_batch(hs, p, q), 3)
+    batched, t_batch = timed(lambda: sbc.sbc_count_batch(hs, p, q), 2)
     with sbc.Batch(hs, p, q) as b:
         b.run()
-        replay, t_replay = timed(b.run, 5)
+        replay, t_replay = timed(b.run, 3)
     # the autotuner times a sample of the batch (at most 1,000 graphs)
     n_tune = min(len(hs), 1000)
     t0 = time.perf_counter()
-    tune = sbc.sbc_autotune(hs[:n_tune], p, q)
+    tune = sbc.sbc_autotune(hs[:n_tune], p, q, reps=2)
     t_tune = time.perf_counter() - t0
     with sbc.Batch(hs, p, q, tune=tune) as b:
         b.run()
-        tuned, t_tuned = timed(b.run, 5)
+        tuned, t_tuned = timed(b.run, 3)
     for name, other in (("batched", batched), ("replay", replay), ("tuned", tuned)):
         bad = [i for i in range(len(plain)) if plain[i] != other[i]]
         if bad:
@@ -234,80 +296,90 @@ def batch_leg(sbc, torch, args):
                                  f"(first: {bad[:5]})")
     for h in hs:
         h.close()
-    n = len(gs)
+    n = len(hs)
     return {"graphs": n, "edges": int(edges), "pq": "(3,3)", "generate_s": t_gen,
             "create_s": t_create, "plain_graphs_per_s": n / t_plain,
             "batched_graphs_per_s": n / t_batch, "replay_graphs_per_s": n / t_replay,
             "tuned_replay_graphs_per_s": n / t_tuned, "autotune_s": t_tune,
             "autotune_graphs": n_tune, "tune": tune,
             "batched_vs_plain": t_plain / t_batch, "replay_vs_plain": t_plain / t_replay,
-            "tuned_replay_vs_plain": t_plain / t_tuned, "total_count": sum(plain)}
+            "tuned_replay_vs_plain": t_plain / t_tuned, "total_count": sum(plain),
+            "equal_to_plain": True}
+
+
+def _serve_run(sbc, srv, gids, reqs, arr, want):
+    """Submit `reqs` at arrival times `arr` (seconds from now) from a client
+    thread; wait for all; check each count; return the server's stats."""
+    srv.reset_stats()
+    tickets = [None] * len(reqs)
+    t_base = time.perf_counter()
+
+    def client():
+        for i, ((g, pq), a) in enumerate(zip(reqs, arr)):
+            dt = t_base + a - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = srv.submit(gids[g], *pq)
+
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    for i, (g, pq) in enumerate(reqs):
+        c, _ = srv.wait(tickets[i])
+        assert c == want[(g, pq)]  # the same count alone and in the mix
+    return srv.stats()
 
 
 def serve_leg(sbc, torch, args):
     """Poisson-arriving requests (graph, p, q) on resident graphs: p50/p99
-    latency and throughput of the server versus one-at-a-time serving of the
-    same arrivals (a FIFO queue over each request's measured standalone time)."""
-    import threading
-
+    latency and throughput of the server (continuous batching over lanes,
+    fused small-graph requests) against a server that serves one request at a
+    time with the plain path (one lane, no fusing), on the same arrivals."""
     import sbc_synth
 
+    t0 = time.perf_counter()
     gs = sbc_synth.batch_graphs(5, args.serve_graphs, 1e3, args.serve_max_edges)
+    t_gen = time.perf_counter() - t0
     hs = [sbc.graph_from_synth(g) for g in gs]
+    edges = int(sum(g.m for g in gs))
+    del gs
     pqs = [(3, 3), (3, 4), (4, 4)]
     rng = np.random.default_rng(5)
-    reqs = [(int(rng.integers(len(hs))), pqs[int(rng.integers(3))]) for _ in range(args.serve_requests)]
-    # standalone service times (one request at a time, warmed)
-    service = {}
-    for g, pq in set(reqs):
-        sbc.sbc_count(hs[g], *pq)
-    for g, pq in set(reqs):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        service[(g, pq)] = sbc.sbc_count(hs[g], *pq)
-        service[(g, pq)] = (service[(g, pq)], time.perf_counter() - t)
+    want = {}
+    t0 = time.perf_counter()
+    for i, h in enumerate(hs):
+        for pq in pqs:
+            want[(i, pq)] = sbc.sbc_count(h, *pq)
+    t_all = time.perf_counter() - t0  # every (graph, p, q) once, one at a time
     out = []
-    with sbc.Server(mem_budget_bytes=int(args.serve_budget_gb * 2**30)) as srv:
+    budget = int(args.serve_budget_gb * 2**30)
+    with sbc.Server(mem_budget_bytes=budget) as srv, \
+            sbc.Server(mem_budget_bytes=budget, lanes=1, max_batch=1) as one:
         gids = [srv.add_graph(h) for h in hs]
+        gids1 = [one.add_graph(h) for h in hs]
         for rate in args.serve_rates:
-            arr = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
-            # one at a time: Lindley recursion over measured service times
-            fin, lat1 = 0.0, []
-            for (g, pq), a in zip(reqs, arr):
-                start = max(a, fin)
-                fin = start + service[(g, pq)][1]
-                lat1.append(fin - a)
-            span1 = fin - arr[0]
-            srv.reset_stats()
-            tickets = [None] * len(reqs)
-            t_base = time.perf_counter()
-
-            def client():
-                for i, ((g, pq), a) in enumerate(zip(reqs, arr)):
-                    dt = t_base + a - time.perf_counter()
-                    if dt > 0:
-                        time.sleep(dt)
-                    tickets[i] = srv.submit(gids[g], *pq)
-
-            th = threading.Thread(target=client)
-            th.start()
-            th.join()
-            lat = []
-            for i, (g, pq) in enumerate(reqs):
-                c, l = srv.wait(tickets[i])
-                assert c == service[(g, pq)][0]  # same count alone and in the mix
-                lat.append(l)
-            st = srv.stats()
-            out.append({"rate_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                        "throughput_rps": st["throughput_rps"], "jobs": st["jobs"],
-                        "fused_requests": st["fused_requests"],
-                        "one_at_a_time": {"p50_ms": 1e3 * float(np.percentile(lat1, 50)),
-                                          "p99_ms": 1e3 * float(np.percentile(lat1, 99)),
-                                          "throughput_rps": len(reqs) / span1}})
+            n = int(min(args.serve_requests, max(200, rate * args.serve_seconds)))
+            reqs = [(int(rng.integers(len(hs))), pqs[int(rng.integers(3))]) for _ in range(n)]
+            arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
+            st = _serve_run(sbc, srv, gids, reqs, arr, want)
+            # the one-at-a-time server saturates early; it serves a prefix of
+            # the same arrivals (its queue only grows, so the prefix's
+            # latencies understate the full run's)
+            n1 = min(n, args.serve_baseline_requests)
+            st1 = _serve_run(sbc, one, gids1, reqs[:n1], arr[:n1], want)
+            out.append({"rate_per_s": rate, "requests": n, "p50_ms": st["p50_ms"],
+                        "p99_ms": st["p99_ms"], "throughput_rps": st["throughput_rps"],
+                        "jobs": st["jobs"], "fused_requests": st["fused_requests"],
+                        "peak_admitted_gb": st["peak_admitted_bytes"] / 2**30,
+                        "one_at_a_time": {"requests": n1, "p50_ms": st1["p50_ms"],
+                                          "p99_ms": st1["p99_ms"],
+                                          "throughput_rps": st1["throughput_rps"]}})
     for h in hs:
         h.close()
-    return {"graphs": len(gs), "edges": int(sum(g.m for g in gs)), "requests": len(reqs),
-            "pq": "(3,3)|(3,4)|(4,4) uniform", "budget_gb": args.serve_budget_gb, "rates": out}
+    return {"graphs": len(hs), "edges": edges, "max_edges": args.serve_max_edges,
+            "generate_s": t_gen, "all_pairs_once_s": t_all,
+            "pq": "(3,3)|(3,4)|(4,4) uniform", "budget_gb": args.serve_budget_gb,
+            "rates": out}
 
 
 def _leg(fn, *a):
@@ -382,6 +454,8 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    # the integer-ALU rates of this GPU at the clocks of this run
+    alu = sbc.sbc_measure_alu_rates(stream=stream)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             flush.zero_()  # L2 flush, outside the timed events
@@ -400,7 +474,7 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
-    launches = sbc.sbc_launch_count() - launches0
+    launches = sbc.sbc_launch_count() - launches0 - 8  # the 8 ALU-rate launches
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms33 = [a.elapsed_time(b) for a, b in ev33]
     ms = float(np.sum(step_ms))
@@ -421,42 +495,54 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     value = tuples_total / (ms_per_step / 1000.0)
 
-    # roofline of the dominant kernel (the tuple / type-count kernel)
+    # rooflines of the step's kernels; "roofline" is the one with most time
     peaks, peak_kind = measured_peaks()
-    tup_ms = [sum(s["ms_tuples"] for s in sts) for sts in per_step_stats]
-    hop_ms = [sum(s["ms_twohop"] for s in sts) for sts in per_step_stats]
-    popc = sum(s["popc_words"] for s in per_step_stats[0])
-    nlaunch = len(PQ)
-    avg_launch_ms = float(np.mean(tup_ms)) / nlaunch
-    achieved = (popc / nlaunch) / (avg_launch_ms / 1000.0) / 1e12
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak = sm_count * POPC_PER_CLK_PER_SM * clk * 1e6 / 1e12
-    roof = {"kernel": "k_tuples (tuple enumeration, AND/POPC type counts)", "bound": "alu",
-            "achieved": achieved, "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak,
-            "traffic": TUPLE_TRAFFIC.get(WORKLOAD) if PQ == [(3, 3), (4, 4)] else None,
-            "peak_basis": f"{sm_count} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {clk:.0f} MHz "
-                          f"(median SM clock sampled under load)",
-            "share_of_step": float(np.mean(tup_ms) / np.mean(step_ms))}
-
-    # the 2-hop kernels (second in the step): algorithmic bytes = one 4-byte
-    # B entry per visited wedge + A_ent, A_pos and the compact bit index of
-    # every anchor-side edge (12 B per edge), against the measured copy peak
+    nl = len(PQ)
+    mean = lambda key: float(np.mean([sum(s[key] for s in sts) for sts in per_step_stats]))
+    t_tup, t_hop, t_tc = mean("ms_tuples"), mean("ms_twohop"), mean("ms_tc")
     s_first = per_step_stats[0]
-    hop_bytes = [4 * s["wedges"] + 12 * g.m for s in s_first]
-    hop_gbs = sum(hop_bytes) / (float(np.mean(hop_ms)) / 1000.0) / 1e9
-    roof_hop = {"kernel": "k_twohop_large + k_twohop_small (2-hop candidates)", "bound": "hbm",
-                "achieved": hop_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": hop_gbs / peaks["hbm_gbs"], "traffic": None,
-                "bytes_per_step": int(sum(hop_bytes)),
-                "note": "gather over the oriented CSR; the 2M-edge graph's structures (~40 MB) "
-                        "stay in L2, so this is an L2-served rate quoted against HBM peak"}
+    popc = sum(s["popc_words"] for s in s_first)
+    popc_peak = alu["popc_per_s"] / 1e12
+    tup_ach = popc / (t_tup / 1000.0) / 1e12 if t_tup > 0 else 0.0
+    roofs = {
+        "k_tuples": {"kernel": "k_tuples (tuple enumeration, AND/POPC type counts)",
+                     "bound": "alu", "achieved": tup_ach, "peak": popc_peak, "unit": "Tpopc/s",
+                     "frac": tup_ach / popc_peak, "ms": t_tup, "launches": nl,
+                     "traffic": TRAFFIC.get(("k_tuples", WORKLOAD)),
+                     "peak_basis": f"POPC rate measured in this run by sbc_measure_alu_rates "
+                                   f"({alu['popc_per_s'] / 1e12:.2f} T/s; LOP3 "
+                                   f"{alu['lop3_per_s'] / 1e12:.2f} T/s)"},
+    }
+    kb = sum(s.get("tc_kblocks", 0) for s in s_first)
+    if kb and t_tc > 0:
+        flops = 2.0 * kb * 128 * 256 * 128
+        tc_ach = flops / (t_tc / 1000.0) / 1e12
+        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
+        tc_peak = 2.0 * bf16  # fp8 dense = 2 x bf16 dense (nominal 4.5 / 2.25 PF)
+        roofs["k_tcpairs"] = {
+            "kernel": "k_zexpand + k_tcpairs (tensor-core pair counts, tcgen05 kind::f8f6f4)",
+            "bound": "tensor", "achieved": tc_ach, "peak": tc_peak, "unit": "TFLOP/s",
+            "frac": tc_ach / tc_peak, "ms": t_tc, "traffic": TRAFFIC.get(("k_tcpairs", WORKLOAD)),
+            "flops_per_step": flops, "tiles": sum(s.get("tc_tiles", 0) for s in s_first),
+            "peak_basis": "2 x measured sustained bf16 TFLOP/s (fp8 is twice bf16 nominally)"}
+    # 2-hop: one 4-byte B entry per visited wedge + A_ent, A_pos and the bit
+    # index of every anchor-side edge (12 B per edge)
+    hop_bytes = sum(4 * s["wedges"] + 12 * g.m for s in s_first)
+    hop_gbs = hop_bytes / (t_hop / 1000.0) / 1e9
+    roofs["k_twohop"] = {"kernel": "k_twohop_large + k_twohop_small (2-hop candidates)",
+                         "bound": "hbm", "achieved": hop_gbs, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": hop_gbs / peaks["hbm_gbs"], "ms": t_hop,
+                         "traffic": TRAFFIC.get(("k_twohop", WORKLOAD)),
+                         "bytes_per_step": int(hop_bytes)}
+    dominant = max(roofs, key=lambda k: roofs[k]["ms"])
+    roof = dict(roofs[dominant])
+    roof["share_of_step"] = roof["ms"] / float(np.mean(step_ms))
 
     # end to end through the public API with pinned host buffers
     h_off = torch.from_numpy(g.offsets).pin_memory()
     h_col = torch.from_numpy(g.cols).pin_memory()
     h_sgn = torch.from_numpy(g.signs).pin_memory()
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, args.e2e_steps))
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(e2e_steps)]
     with torch.cuda.stream(stream):
@@ -475,16 +561,25 @@ def run_ours(args):
     h2d = g.offsets.nbytes + g.cols.nbytes + g.signs.nbytes
     e2e = {"value": tuples_total / (e2e_ms / 1000.0), "unit": "anchor tuples/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 * len(PQ),
-           "ms_per_step": e2e_ms}
+           "ms_per_step": e2e_ms, "steps": e2e_steps}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        tup, dt, na, cores = oracle_sample(g, 3, 3, args.cpu_frac, 7)
-        cpu = {"value": tup / dt, "unit": "anchor tuples/s", "cores": cores, "kind": "oracle",
-               "sample": f"(3,3) on a seeded random {args.cpu_frac:.1%} sample of U anchors "
-                         f"({na} anchors, {tup} tuples, {dt:.1f} s)"}
+        import oracle
 
-    batch = serve = None
+        side = anchor_side(g)
+        p, q = PQ[0]
+        with oracle.Prepared(g, side) as prep:
+            tup, dt, na, cores = oracle_sample(prep, g, side, p, q, args.cpu_frac, 7)
+        cpu = {"value": tup / dt, "unit": "anchor tuples/s", "cores": cores, "kind": "oracle",
+               "sample": f"({p},{q}) on a seeded random {args.cpu_frac:.3%} sample of "
+                         f"{'U' if side == 0 else 'V'} anchors ({na} anchors, {tup} tuples, "
+                         f"{dt:.1f} s; graph lists built once beforehand)",
+               "seconds_to_exact_33_estimate": dt / args.cpu_frac}
+
+    medium = batch = serve = None
+    if rank == 0 and ws == 1 and not args.no_medium:
+        medium = _leg(medium_leg, sbc, torch, args)
     if rank == 0 and ws == 1 and args.batch_graphs > 0:
         batch = _leg(batch_leg, sbc, torch, args)
     if rank == 0 and ws == 1 and args.serve_requests > 0:
@@ -496,21 +591,23 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "anchor tuples/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
-            "dtype": "u32/u64 integer (exact u128 counts)", "data": "synthetic",
+            "dtype": "u32/u64 integer masks, fp8 0/1 tensor-core operands (exact u128 counts)",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "pq": "+".join(f"({p},{q})" for p, q in PQ),
-                       "n_u": g.n_u, "n_v": g.n_v,
-                       "edges": g.m, "seed": 2, "l2": "flushed between steps (512 MiB write)",
+                       "n_u": g.n_u, "n_v": g.n_v, "edges": g.m,
+                       "l2": "inputs (1.1 GB on the device) larger than L2, and flushed "
+                             "between steps (512 MiB write)",
                        "parallelism": f"anchor shards x{ws}" if ws > 1 else "1 GPU"},
             "seconds_to_exact_33": ms33_tot / args.steps / 1000.0,
             "counts": totals, "anchor_tuples": {str(k): v for k, v in tuples.items()},
-            "phase_ms": {"tuples": float(np.mean(tup_ms)), "twohop": float(np.mean(hop_ms)),
-                         "other": float(np.mean(step_ms) - np.mean(tup_ms) - np.mean(hop_ms))},
+            "phase_ms": {"tuples": t_tup, "tensor_core_pairs": t_tc, "twohop": t_hop,
+                         "other": float(np.mean(step_ms)) - t_tup - t_tc - t_hop},
             "tuples_tested": [s["tuples_tested"] for s in s0],
             "tuples_typed": [s["tuples_typed"] for s in s0],
-            "roofline": roof, "roofline_twohop": roof_hop, "peak_source": peak_kind,
-            "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
-            "cpu_baseline": cpu,
-            "batch": batch, "serve": serve,
+            "tc_anchors": [s.get("tc_anchors", 0) for s in s0],
+            "roofline": roof, "roofline_kernels": roofs, "peak_source": peak_kind,
+            "alu_rates": alu, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
+            "cpu_baseline": cpu, "medium": medium, "batch": batch, "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -527,20 +624,30 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
-    ap.add_argument("--batch-graphs", type=int, default=1000,
-                    help="graphs of the batch leg (0 skips it; the full batch is 10000)")
-    ap.add_argument("--serve-graphs", type=int, default=100)
-    ap.add_argument("--serve-max-edges", type=float, default=1e5)
-    ap.add_argument("--serve-requests", type=int, default=2000, help="0 skips the serving leg")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[100.0, 1000.0, 5000.0])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-medium", action="store_true", help="skip the 2M-edge leg")
+    ap.add_argument("--batch-graphs", type=int, default=10000,
+                    help="graphs of the batch leg (0 skips it; the full recipe is 10000)")
+    ap.add_argument("--serve-graphs", type=int, default=500)
+    ap.add_argument("--serve-max-edges", type=float, default=1e6,
+                    help="largest graph of the serving leg (the recipe's 1e7-edge graphs take "
+                         "minutes to hours per (4,4) request)")
+    ap.add_argument("--serve-requests", type=int, default=50000,
+                    help="most requests per rate (0 skips the serving leg)")
+    ap.add_argument("--serve-seconds", type=float, default=1.0,
+                    help="arrival span per rate: requests = min(serve-requests, rate x this)")
+    ap.add_argument("--serve-rates", type=float, nargs="+",
+                    default=[100.0, 1000.0, 5000.0, 20000.0])
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
+    ap.add_argument("--serve-baseline-requests", type=int, default=2000,
+                    help="requests (a prefix of each rate's arrivals) served one at a time")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
-                    help="graph to count (default: the 200k x 100k x 2M workload)")
+                    help="graph to count (default: the 5M x 1M x 60M workload)")
     ap.add_argument("--pq", action="append", default=None,
-                    help="p,q pair to count (repeatable); default 3,3 and 4,4")
-    ap.add_argument("--cpu-frac", type=float, default=0.10,
+                    help="p,q pair to count (repeatable); default 3,3")
+    ap.add_argument("--cpu-frac", type=float, default=0.0005,
                     help="anchor sample fraction for the oracle CPU baseline")
-    ap.add_argument("--ref-frac", type=float, default=0.02,
+    ap.add_argument("--ref-frac", type=float, default=0.0001,
                     help="anchor sample fraction per step for --impl reference")
     args = ap.parse_args()
     WORKLOAD = args.workload

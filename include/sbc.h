@@ -336,6 +336,17 @@ sbc_status sbc_count_csr_noalloc(int64_t n_u, int64_t n_v, int64_t nnz, const vo
                                  const int32_t *cols, const void *signs, uint32_t flags, int p,
                                  int q, sbc_u128 *out, void *stream);
 
+/*
+ * Measurement helper (no counterpart in the paper): the current device's
+ * sustained rates of 32-bit population counts and of three-input logic
+ * operations (LOP3), the operations of the tuple step's mask tests, in
+ * operations per second. Each is the best of three timed launches (CUDA
+ * events on `stream`, after one warm-up launch) of a kernel that keeps every
+ * SM busy with eight independent dependency chains per thread; about 30 ms in
+ * all. Synchronises `stream`.
+ */
+sbc_status sbc_measure_alu_rates(double *popc_per_s, double *lop3_per_s, void *stream);
+
 /* Human-readable message for the last non-OK status on this thread. */
 const char *sbc_last_error(void);
 

@@ -58,6 +58,18 @@ def _declare(lib):
         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_void_p,
         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
     ]
+    lib.sbc_oracle_prepare.restype = ctypes.c_void_p
+    lib.sbc_oracle_prepare.argtypes = [
+        ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+    ]
+    lib.sbc_oracle_count_prepared.restype = ctypes.c_int
+    lib.sbc_oracle_count_prepared.argtypes = [
+        ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_void_p,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+    ]
+    lib.sbc_oracle_release.restype = None
+    lib.sbc_oracle_release.argtypes = [ctypes.c_void_p]
     lib.sbc_oracle_brute.restype = ctypes.c_int
     lib.sbc_oracle_brute.argtypes = [
         ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -99,6 +111,43 @@ def _u128(lo, hi) -> int:
     return int(lo) | (int(hi) << 64)
 
 
+class Prepared:
+    """The graph's lists built once for one anchor side, for repeated counts
+    (for example, timed anchor samples of a large graph). Use as a context
+    manager or call close()."""
+
+    def __init__(self, g, side: int, lib=None):
+        self.lib = _load() if lib is None else lib
+        self.g = g
+        self.side = side
+        rc = ctypes.c_int(0)
+        self._keep = (np.ascontiguousarray(g.offsets, dtype=np.int64),
+                      np.ascontiguousarray(g.cols, dtype=np.int32),
+                      np.ascontiguousarray(g.signs, dtype=np.int8))
+        off, col, sgn = self._keep
+        self.h = self.lib.sbc_oracle_prepare(g.n_u, g.n_v, off.ctypes.data, col.ctypes.data,
+                                             sgn.ctypes.data, side, ctypes.byref(rc))
+        if not self.h:
+            raise RuntimeError(f"oracle prepare failed with code {rc.value}")
+
+    def count(self, p: int, q: int, threads: int = 0, per_anchor: bool = False,
+              with_tuples: bool = False, anchors=None, max_subsets: int = 0, skipped=None):
+        """Same results as `count` (module function) on this side."""
+        return _count_call(self.lib, self.g, self.side, p, q, threads, per_anchor, with_tuples,
+                           anchors, max_subsets, skipped, prepared=self.h)
+
+    def close(self):
+        if self.h:
+            self.lib.sbc_oracle_release(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
           per_anchor: bool = False, with_tuples: bool = False, lib=None, anchors=None,
           max_subsets: int = 0, skipped=None):
@@ -119,6 +168,12 @@ def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
     lib = _load() if lib is None else lib
     if side is None:
         side = default_side(g.n_u, g.n_v)
+    return _count_call(lib, g, side, p, q, threads, per_anchor, with_tuples, anchors,
+                       max_subsets, skipped)
+
+
+def _count_call(lib, g, side, p, q, threads, per_anchor, with_tuples, anchors, max_subsets,
+                skipped, prepared=None):
     off = np.ascontiguousarray(g.offsets, dtype=np.int64)
     col = np.ascontiguousarray(g.cols, dtype=np.int32)
     sgn = np.ascontiguousarray(g.signs, dtype=np.int8)
@@ -131,12 +186,16 @@ def count(g, p: int, q: int, side: int | None = None, threads: int = 0,
     if anchors is not None:
         mask = np.zeros(max(n_s, 1), dtype=np.uint8)
         mask[np.asarray(list(anchors), dtype=np.int64)] = 1
-    rc = lib.sbc_oracle_count(
-        g.n_u, g.n_v, off.ctypes.data, col.ctypes.data, sgn.ctypes.data, p, q, side, threads,
-        out, anc.ctypes.data if anc is not None else None, ctypes.addressof(tup),
-        mask.ctypes.data if mask is not None else None, max_subsets,
-        skip.ctypes.data if skip is not None else None,
-    )
+    anc_p = anc.ctypes.data if anc is not None else None
+    mask_p = mask.ctypes.data if mask is not None else None
+    skip_p = skip.ctypes.data if skip is not None else None
+    if prepared is not None:
+        rc = lib.sbc_oracle_count_prepared(prepared, p, q, threads, out, anc_p,
+                                           ctypes.addressof(tup), mask_p, max_subsets, skip_p)
+    else:
+        rc = lib.sbc_oracle_count(g.n_u, g.n_v, off.ctypes.data, col.ctypes.data,
+                                  sgn.ctypes.data, p, q, side, threads, out, anc_p,
+                                  ctypes.addressof(tup), mask_p, max_subsets, skip_p)
     if skip is not None and skipped is not None:
         skipped.update(np.nonzero(skip)[0].tolist())
     if rc == 1:

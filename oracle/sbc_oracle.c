@@ -356,36 +356,64 @@ static u128 extend(ctx_t *c, int d, const nent_t *n, int64_t nn, int32_t last) {
     return b;
 }
 
-/*
- * Count on anchor side S (lists `s`, by id) against the other side `o`.
- * p = set size on S, q = subset size on the other side.
- */
-static int count_side(const side_t *s, side_t *o, int p, int q, int nthreads,
-                      const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped,
-                      uint64_t out[2], uint64_t *anchor_out, uint64_t *tuples_out, int *ovf_out) {
+/* The graph's lists, ordered for one anchor side: the anchor side's lists
+ * by id, the other side's by the anchor side's priority rank. */
+typedef struct {
+    side_t su, sv;
+    int side;
+    int64_t *deg, *rank; /* of the anchor side's vertices */
+} prep_t;
+
+static void free_prep(prep_t *P) {
+    free_side(&P->su);
+    free_side(&P->sv);
+    free(P->deg);
+    free(P->rank);
+    memset(P, 0, sizeof(*P));
+}
+
+/* Orders the lists for anchor side `side` and ranks its vertices by rho. */
+static int order_for_side(prep_t *P, int side) {
+    side_t *s = side == 0 ? &P->su : &P->sv, *o = side == 0 ? &P->sv : &P->su;
     int64_t nS = s->n;
-    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nS > 0 ? nS : 1));
-    int64_t *rank = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nS > 0 ? nS : 1));
+    P->side = side;
+    P->deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nS > 0 ? nS : 1));
+    P->rank = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nS > 0 ? nS : 1));
     adj_t *ord = (adj_t *)malloc(sizeof(adj_t) * (size_t)(nS > 0 ? nS : 1));
     int64_t *key = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nS > 0 ? nS : 1));
-    if (!deg || !rank || !ord || !key) {
-        free(deg), free(rank), free(ord), free(key);
+    if (!P->deg || !P->rank || !ord || !key) {
+        free(ord), free(key);
         return -1;
     }
     /* Definition 4: rho orders by degree, then by id */
     for (int64_t x = 0; x < nS; x++) {
-        deg[x] = s->off[x + 1] - s->off[x];
-        key[x] = deg[x] * (nS + 1) + x;
+        P->deg[x] = s->off[x + 1] - s->off[x];
+        key[x] = P->deg[x] * (nS + 1) + x;
         ord[x].id = (int32_t)x;
     }
     g_key = key;
     qsort(ord, (size_t)nS, sizeof(adj_t), cmp_by_key);
-    for (int64_t i = 0; i < nS; i++) rank[ord[i].id] = i;
+    for (int64_t i = 0; i < nS; i++) P->rank[ord[i].id] = i;
     /* the other side's lists in increasing rank, the anchor side's by id */
     for (int64_t v = 0; v < o->n; v++)
         qsort(o->adj + o->off[v], (size_t)(o->off[v + 1] - o->off[v]), sizeof(adj_t), cmp_by_key);
+    for (int64_t x = 0; x < nS; x++)
+        qsort(s->adj + s->off[x], (size_t)(s->off[x + 1] - s->off[x]), sizeof(adj_t), cmp_by_id);
     free(ord);
     free(key);
+    return 0;
+}
+
+/*
+ * Count on the prepared anchor side S against the other side.
+ * p = set size on S, q = subset size on the other side.
+ */
+static int count_side(const prep_t *P, int p, int q, int nthreads,
+                      const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped,
+                      uint64_t out[2], uint64_t *anchor_out, uint64_t *tuples_out, int *ovf_out) {
+    const side_t *s = P->side == 0 ? &P->su : &P->sv, *o = P->side == 0 ? &P->sv : &P->su;
+    const int64_t *deg = P->deg, *rank = P->rank;
+    int64_t nS = s->n;
 
     int nt = 1;
 #ifdef _OPENMP
@@ -478,8 +506,6 @@ static int count_side(const side_t *s, side_t *o, int p, int q, int nthreads,
     }
     free(part);
     free(tup);
-    free(deg);
-    free(rank);
     out[0] = (uint64_t)total;
     out[1] = (uint64_t)(total >> 64);
     if (tuples_out) {
@@ -524,12 +550,11 @@ static int edges_of(int64_t n_u, int64_t n_v, const int64_t *off, const int32_t 
  * exceeds it are left out and flagged in `skipped` (one byte per vertex).
  * Returns 0, -1 on allocation failure, -2 on bad arguments, 1 on overflow.
  */
-int sbc_oracle_count(int64_t n_u, int64_t n_v, const int64_t *off, const int32_t *col,
-                     const int8_t *sgn, int p_u, int q_v, int anchor_side, int nthreads,
-                     uint64_t out[2], uint64_t *anchor_out, uint64_t *tuples_out,
-                     const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped) {
-    if (p_u < 2 || q_v < 2 || p_u > 16 || q_v > 16 || n_u < 0 || n_v < 0 || n_u >= INT32_MAX ||
-        n_v >= INT32_MAX)
+static int prepare(prep_t *P, int64_t n_u, int64_t n_v, const int64_t *off, const int32_t *col,
+                   const int8_t *sgn, int anchor_side) {
+    memset(P, 0, sizeof(*P));
+    if (n_u < 0 || n_v < 0 || n_u >= INT32_MAX || n_v >= INT32_MAX ||
+        (anchor_side != 0 && anchor_side != 1))
         return -2;
     int32_t *ru = NULL;
     int rc = edges_of(n_u, n_v, off, col, sgn, &ru);
@@ -538,30 +563,88 @@ int sbc_oracle_count(int64_t n_u, int64_t n_v, const int64_t *off, const int32_t
         return rc;
     }
     int64_t m = off[n_u];
-    side_t su, sv;
-    memset(&su, 0, sizeof(su));
-    memset(&sv, 0, sizeof(sv));
-    if (build_lists(n_u, m, ru, col, sgn, &su) || build_lists(n_v, m, col, ru, sgn, &sv)) {
+    if (build_lists(n_u, m, ru, col, sgn, &P->su) || build_lists(n_v, m, col, ru, sgn, &P->sv) ||
+        order_for_side(P, anchor_side)) {
         free(ru);
-        free_side(&su);
-        free_side(&sv);
+        free_prep(P);
         return -1;
     }
     free(ru);
-    side_t *s = anchor_side == 0 ? &su : &sv, *o = anchor_side == 0 ? &sv : &su;
-    for (int64_t x = 0; x < s->n; x++)
-        qsort(s->adj + s->off[x], (size_t)(s->off[x + 1] - s->off[x]), sizeof(adj_t), cmp_by_id);
+    return 0;
+}
+
+static int count_prepared(const prep_t *P, int p_u, int q_v, int nthreads, uint64_t out[2],
+                          uint64_t *anchor_out, uint64_t *tuples_out, const uint8_t *anchor_mask,
+                          uint64_t max_subsets, uint8_t *skipped) {
+    if (p_u < 2 || q_v < 2 || p_u > 16 || q_v > 16) return -2;
     int ovf = 0;
-    if (anchor_side == 0)
-        rc = count_side(s, o, p_u, q_v, nthreads, anchor_mask, max_subsets, skipped, out,
-                        anchor_out, tuples_out, &ovf);
-    else
-        rc = count_side(s, o, q_v, p_u, nthreads, anchor_mask, max_subsets, skipped, out,
-                        anchor_out, tuples_out, &ovf);
-    free_side(&su);
-    free_side(&sv);
+    int rc = P->side == 0 ? count_side(P, p_u, q_v, nthreads, anchor_mask, max_subsets, skipped,
+                                       out, anchor_out, tuples_out, &ovf)
+                          : count_side(P, q_v, p_u, nthreads, anchor_mask, max_subsets, skipped,
+                                       out, anchor_out, tuples_out, &ovf);
     if (rc) return rc;
     return ovf ? 1 : 0;
+}
+
+/*
+ * Count balanced bicliques with p_u vertices from U and q_v from V.
+ *   anchor_side 0: L drawn from U (set size p_u, subsets of V of size q_v)
+ *   anchor_side 1: L drawn from V (set size q_v, subsets of U of size p_u)
+ * off/col/sgn: CSR over U, signs +1/-1. out: u128 total as {lo, hi}.
+ * anchor_out (optional): each anchor's share (the sets whose member of lowest
+ * priority it is), 2 u64 per vertex of the anchor side.
+ * tuples_out (optional): sum over anchors u of binom(|C(u)|, p-1), C(u) the
+ * vertices of higher priority sharing at least q neighbours with u (the
+ * number of subsets Algorithm 2 enumerates), {lo, hi}.
+ * anchor_mask (optional): one byte per anchor-side vertex; only anchors with
+ * a non-zero byte are processed (the total then covers those anchors only).
+ * max_subsets (test option, 0 = none): anchors whose binom(|C(u)|, p-1)
+ * exceeds it are left out and flagged in `skipped` (one byte per vertex).
+ * Returns 0, -1 on allocation failure, -2 on bad arguments, 1 on overflow.
+ */
+int sbc_oracle_count(int64_t n_u, int64_t n_v, const int64_t *off, const int32_t *col,
+                     const int8_t *sgn, int p_u, int q_v, int anchor_side, int nthreads,
+                     uint64_t out[2], uint64_t *anchor_out, uint64_t *tuples_out,
+                     const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped) {
+    if (p_u < 2 || q_v < 2 || p_u > 16 || q_v > 16) return -2;
+    prep_t P;
+    int rc = prepare(&P, n_u, n_v, off, col, sgn, anchor_side);
+    if (rc) return rc;
+    rc = count_prepared(&P, p_u, q_v, nthreads, out, anchor_out, tuples_out, anchor_mask,
+                        max_subsets, skipped);
+    free_prep(&P);
+    return rc;
+}
+
+/* The same count over lists built once (sbc_oracle_prepare) for repeated
+ * counts of one graph from one anchor side, e.g. anchor samples. */
+void *sbc_oracle_prepare(int64_t n_u, int64_t n_v, const int64_t *off, const int32_t *col,
+                         const int8_t *sgn, int anchor_side, int *rc) {
+    prep_t *P = (prep_t *)malloc(sizeof(prep_t));
+    if (!P) {
+        *rc = -1;
+        return NULL;
+    }
+    *rc = prepare(P, n_u, n_v, off, col, sgn, anchor_side);
+    if (*rc) {
+        free(P);
+        return NULL;
+    }
+    return P;
+}
+
+int sbc_oracle_count_prepared(void *h, int p_u, int q_v, int nthreads, uint64_t out[2],
+                              uint64_t *anchor_out, uint64_t *tuples_out,
+                              const uint8_t *anchor_mask, uint64_t max_subsets, uint8_t *skipped) {
+    if (!h) return -2;
+    return count_prepared((const prep_t *)h, p_u, q_v, nthreads, out, anchor_out, tuples_out,
+                          anchor_mask, max_subsets, skipped);
+}
+
+void sbc_oracle_release(void *h) {
+    if (!h) return;
+    free_prep((prep_t *)h);
+    free(h);
 }
 
 /* Next k-subset of {0..n-1} in lexicographic order; 0 when done. */

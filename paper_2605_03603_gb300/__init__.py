@@ -173,6 +173,17 @@ _declare("sbc_server_wait", ctypes.c_int,
 _declare("sbc_server_stats", ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)])
 _declare("sbc_server_reset_stats", ctypes.c_int, [_vp])
 _declare("sbc_server_destroy", ctypes.c_int, [_vp])
+_declare("sbc_measure_alu_rates", ctypes.c_int,
+         [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp])
+
+
+def sbc_measure_alu_rates(stream=None) -> dict:
+    """Measured POPC and LOP3 rates of the current device (operations/s)."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib.sbc_measure_alu_rates(ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)))
+    return {"popc_per_s": a.value, "lop3_per_s": b.value}
+
+
 _declare("sbc_count_csr_noalloc", ctypes.c_int,
          [_i64, _i64, _i64, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
           ctypes.POINTER(U128), _vp])

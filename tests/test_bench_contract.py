@@ -10,8 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_json_line():
     out = subprocess.run(
-        [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-         "--warmup", "3", "--ref-frac", "0.002"],
+        [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+         "--warmup", "3", "--ref-frac", "0.2", "--workload", "plain-2k-1.5k-20k"],
         capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
@@ -25,4 +25,6 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert d["config"]["workload"] == "plain-200k-100k-2M"
+    assert d["config"]["workload"] == "plain-2k-1.5k-20k"
+    assert d["config"]["pq"] == "(3,3)"
+    assert d["seconds_to_exact_33_estimate"] > 0

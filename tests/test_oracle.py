@@ -452,3 +452,19 @@ def test_pins_pass_on_oracle():
 def test_pins_catch_planted_mistakes(mutant, tmp_path):
     lib = oracle.mutant(mutant, str(tmp_path))
     assert not _pins_pass(lib)
+
+
+def test_prepared_lists_count_the_same():
+    """The prepared form (lists built once, counted many times, as the
+    benchmark's CPU legs use it) gives the plain call's results."""
+    g = sbc_synth.plain_small()
+    rng = np.random.default_rng(3)
+    for side in (0, 1):
+        n_s = g.n_u if side == 0 else g.n_v
+        sample = np.nonzero(rng.random(n_s) < 0.3)[0]
+        with oracle.Prepared(g, side) as prep:
+            for p, q in [(3, 3), (4, 3), (3, 4)]:
+                want = oracle.count(g, p, q, side=side, per_anchor=True, with_tuples=True)
+                assert prep.count(p, q, per_anchor=True, with_tuples=True) == want
+                assert (prep.count(p, q, anchors=sample, with_tuples=True) ==
+                        oracle.count(g, p, q, side=side, anchors=sample, with_tuples=True))
