@@ -108,7 +108,10 @@ typedef struct {
 sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
 
 /* Anchor side choice (Algorithm 2 anchors on a side S; see sbc_count_opts). */
-#define SBC_SIDE_AUTO (-1) /* the side with fewer 2-paths to visit (ties: U) */
+#define SBC_SIDE_AUTO (-1) /* the side with fewer 2-paths to visit (ties: U); when p != q and
+                              one side gives tuples of 3 against tuples of 4 or more on the
+                              other, that side (its pairs run on the tensor cores) unless it
+                              visits over 64 times the other side's 2-paths */
 #define SBC_SIDE_U 0       /* anchors in U: tuples of p, q from V */
 #define SBC_SIDE_V 1       /* anchors in V: tuples of q, p from U */
 
@@ -162,8 +165,9 @@ typedef struct {
 typedef struct {
     int32_t anchor_side;  /* SBC_SIDE_AUTO, SBC_SIDE_U or SBC_SIDE_V */
     int32_t flags;        /* SBC_COUNT_* bits, 0 for a plain count */
-    /* optional per-anchor contributions, host memory, n_side entries indexed
-     * by vertex id of the anchor side (n_u or n_v entries), or NULL */
+    /* optional per-anchor contributions, host memory, indexed by vertex id of
+     * the anchor side: n_u entries (side U), n_v (side V), max(n_u, n_v) with
+     * SBC_SIDE_AUTO (sbc_count_stats.anchor_side then tells the side); or NULL */
     sbc_u128 *per_anchor;
     /* first shard of anchors and number of shards: anchors with
      * (rank of the anchor) % shard_count == shard are counted. 0/0 or 0/1 = all. */

@@ -337,16 +337,12 @@ def sbc_count_ex(g: Graph, p: int, q: int, anchor_side: int = SBC_SIDE_AUTO,
         opts.flags |= SBC_COUNT_CHECK
     opts.shard = shard
     opts.shard_count = shard_count
-    n_side = None
     per = None
     if per_anchor:
-        side = anchor_side
-        if side == SBC_SIDE_AUTO:
-            info = sbc_graph_info(g)
-            side = 0 if info["wedges_anchor_u"] <= info["wedges_anchor_v"] else 1
-            opts.anchor_side = side
-        n_side = g.n_u if side == 0 else g.n_v
-        per = np.zeros(2 * max(n_side, 1), dtype=np.uint64)
+        # room for either side when the library picks it
+        n_alloc = (max(g.n_u, g.n_v) if anchor_side == SBC_SIDE_AUTO
+                   else (g.n_u if anchor_side == 0 else g.n_v))
+        per = np.zeros(2 * max(n_alloc, 1), dtype=np.uint64)
         opts.per_anchor = per.ctypes.data
     st = CountStats()
     _check(lib.sbc_count_ex(g.handle, p, q, ctypes.byref(opts), ctypes.byref(st),
@@ -354,6 +350,7 @@ def sbc_count_ex(g: Graph, p: int, q: int, anchor_side: int = SBC_SIDE_AUTO,
     d = st.as_dict()
     pa = None
     if per is not None:
+        n_side = g.n_u if d["anchor_side"] == 0 else g.n_v
         pa = [int(per[2 * i]) | (int(per[2 * i + 1]) << 64) for i in range(n_side)]
     return d["count"], d, pa
 

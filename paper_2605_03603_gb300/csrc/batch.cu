@@ -218,7 +218,7 @@ sbc_batch *batch_create(const sbc_graph *const *gs_in, size_t n, int p, int q, b
         if (gs[i]->device != b->device)
             fail(SBC_E_INVAL, "graph %zu lives on device %d, current device is %d", i, gs[i]->device,
                  b->device);
-        side[i] = gs[i]->wedges_u <= gs[i]->wedges_v ? 0 : 1;
+        side[i] = preferred_side(gs[i], p, q);
         sbc_graph *g = const_cast<sbc_graph *>(gs[i]);
         std::lock_guard<std::mutex> lock(g->mu);
         build_orientation(g, side[i], s);

@@ -2875,7 +2875,7 @@ struct CountRun {
         ia.cnt = cnt.ptr;
         ia.tc_on = spec.tc_min_w >= 0 && R == 2 && !thread_arena_active();
         ia.tc_min_w = spec.tc_min_w > 0 ? (uint32_t)spec.tc_min_w : kTcMinWords;
-        ia.tc_min_nc = kTcMinCandidates;
+        ia.tc_min_nc = tc_min_candidates();
         if (ia.tc_on) {
             tc_list.alloc(nX, s);
             tc_ensure_attrs();
@@ -3091,6 +3091,17 @@ uint32_t hash_slots_cap() {
     return (uint32_t)(v < 32 ? 32 : v);
 }
 
+// Candidates an anchor needs for the tensor-core pair step (tuning override
+// SBC_TC_MIN_CANDIDATES, at least 2).
+uint32_t tc_min_candidates() {
+    uint32_t v = kTcMinCandidates;
+    if (const char *e = getenv("SBC_TC_MIN_CANDIDATES")) {
+        long long x = atoll(e);
+        if (x >= 2 && x < (1ll << 31)) v = (uint32_t)x;
+    }
+    return v;
+}
+
 bool debug_checks_env() {
     const char *e = getenv("SBC_DEBUG");
     return e && *e && *e != '0';
@@ -3113,7 +3124,7 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     SBC_CUDA(cudaGetDevice(&cur));
     if (cur != g->device) fail(SBC_E_INVAL, "graph lives on device %d, current device is %d", g->device, cur);
     int side = opts ? opts->anchor_side : SBC_SIDE_AUTO;
-    if (side == SBC_SIDE_AUTO) side = g->wedges_u <= g->wedges_v ? 0 : 1;
+    if (side == SBC_SIDE_AUTO) side = preferred_side(g, p, q);
     if (side != 0 && side != 1) fail(SBC_E_INVAL, "anchor_side must be -1, 0 or 1");
     CountSpec spec;
     spec.k = side == 0 ? p : q;

@@ -370,4 +370,15 @@ sbc_graph *create_graph(int64_t n_u, int64_t n_v, int64_t nnz, const void *row_o
     return g.release();
 }
 
+int preferred_side(const sbc_graph *g, int p, int q) {
+    const int by_wedges = g->wedges_u <= g->wedges_v ? 0 : 1;
+    // anchoring on U gives tuples of p, on V of q
+    const bool u3 = p == 3 && q >= 4, v3 = q == 3 && p >= 4;
+    if (!u3 && !v3) return by_wedges;
+    const int side3 = u3 ? 0 : 1;
+    const uint64_t w3 = side3 == 0 ? g->wedges_u : g->wedges_v;
+    const uint64_t wo = side3 == 0 ? g->wedges_v : g->wedges_u;
+    return w3 / 64 <= wo ? side3 : by_wedges;
+}
+
 }  // namespace sbc

@@ -172,6 +172,13 @@ int sm_count();
 // Kernel launches issued by the library since load (for reporting).
 extern std::atomic<int64_t> g_launches;
 
+// Anchor side of an automatic count (graph.cu): the side with fewer 2-paths
+// to visit, except that when p != q and exactly one side gives tuples of 3
+// against tuples of 4 or more on the other, that side (whose candidate pairs
+// take the tensor-core step) unless it visits more than 64 times the other
+// side's 2-paths. 0 = U, 1 = V.
+int preferred_side(const sbc_graph *g, int p, int q);
+
 // Upload, validate and prepare a graph (graph.cu).
 sbc_graph *create_graph(int64_t n_u, int64_t n_v, int64_t nnz, const void *row_offsets,
                         const int32_t *cols, const void *signs, uint32_t flags, cudaStream_t s);
@@ -226,6 +233,8 @@ void countrun_destroy(CountRun *r);
 unsigned long long pos_node_cost_setting();
 // SBC_DEBUG set (and not "0") in the environment: self-checks on every count.
 bool debug_checks_env();
+// Candidates an anchor needs for the tensor-core pair step.
+uint32_t tc_min_candidates();
 // SBC_HASH_SLOTS_CAP (tests only): the 2-hop tables' slot cap, 0 for none.
 uint32_t hash_slots_cap();
 // Applies launch parameters (NULL or zero fields: defaults) to a count spec;

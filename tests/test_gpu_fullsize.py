@@ -4,9 +4,8 @@ anchor side and method), and on the 60,000,000-edge workload.
 
 The oracle cannot count the whole graph within a test for (4,4), so:
 * per-anchor contributions of a seeded sample of anchors (uniform, nonzero,
-  and the heaviest) are compared with the oracle computed one anchor at a
-  time (anchors whose Algorithm 2 enumeration exceeds a cap are left out and
-  reported);
+  and the heaviest, uncapped) are compared with the oracle computed for those
+  anchors only;
 * totals are compared through properties that hold at any size: the (3,3)
   count is the same whether the anchors are U or V vertices (side swap), and
   the per-anchor values add up to the total; the full (3,3) total is also
@@ -55,7 +54,7 @@ def sample_anchors(per, rng, n_uniform=120, n_nonzero=120, n_top=12):
     return sorted(pick), top
 
 
-@pytest.mark.parametrize("p,q,cap", [(3, 3, 0), (4, 4, 20_000_000)])
+@pytest.mark.parametrize("p,q,cap", [(3, 3, 0), (4, 4, 0)])
 def test_fullsize_sampled_anchors(sbc, medium, p, q, cap):
     g, h = medium
     total, st, per = sbc.sbc_count_ex(h, p, q, anchor_side=0, per_anchor=True)
@@ -66,7 +65,7 @@ def test_fullsize_sampled_anchors(sbc, medium, p, q, cap):
     _, want = oracle.count(g, p, q, side=0, per_anchor=True, anchors=anchors,
                            max_subsets=cap, skipped=skipped)
     compared = [a for a in anchors if a not in skipped]
-    assert len(compared) >= 200
+    assert len(compared) >= 200 and set(top) <= set(compared)  # the 12 heaviest included
     mism = [(a, per[a], want[a]) for a in compared if per[a] != want[a]]
     assert not mism, mism[:5]
     # the heaviest compared anchors carry a real share of the count
@@ -105,25 +104,43 @@ def large(sbc):
     h.close()
 
 
-def test_large_33_sampled_anchors(sbc, large):
-    """Per-anchor (3,3) contributions of the 60M-edge graph on its preferred
-    anchor side (V) against the oracle one anchor at a time; anchors whose
-    Algorithm 2 enumeration exceeds the cap are left out. Totals: per-anchor
-    values add up to the count."""
-    g, h = large
-    info = sbc.sbc_graph_info(h)
-    side = 0 if info["wedges_anchor_u"] <= info["wedges_anchor_v"] else 1
-    total, st, per = sbc.sbc_count_ex(h, 3, 3, anchor_side=side, per_anchor=True)
-    assert st["anchor_side"] == side
+def _large_sampled(sbc, g, h, p, q, seed, n_top=8):
+    """Per-anchor values of the automatic count for a seeded sample of anchors
+    (uniform, nonzero, the heaviest) against the oracle on the same side,
+    uncapped; per-anchor values add up to the total. Returns (total, side)."""
+    total, st, per = sbc.sbc_count_ex(h, p, q, per_anchor=True)
+    side = st["anchor_side"]
     assert sum(per) == total
-    assert total == sbc.sbc_count(h, 3, 3)
-    rng = np.random.default_rng(333)
-    anchors, _ = sample_anchors(per, rng, n_uniform=100, n_nonzero=150, n_top=8)
-    skipped = set()
-    _, want = oracle.count(g, 3, 3, side=side, per_anchor=True, anchors=anchors,
-                           max_subsets=2_000_000, skipped=skipped)
-    compared = [a for a in anchors if a not in skipped]
-    assert len(compared) >= 150
-    mism = [(a, per[a], want[a]) for a in compared if per[a] != want[a]]
+    rng = np.random.default_rng(seed)
+    anchors, top = sample_anchors(per, rng, n_uniform=100, n_nonzero=150, n_top=n_top)
+    _, want = oracle.count(g, p, q, side=side, per_anchor=True, anchors=anchors)
+    mism = [(a, per[a], want[a]) for a in anchors if per[a] != want[a]]
     assert not mism, mism[:5]
-    assert sum(per[a] for a in compared) > 0
+    assert len(anchors) >= 150 and sum(per[a] for a in anchors) > 0
+    return total, side
+
+
+def test_large_33_sampled_anchors(sbc, large):
+    """(3,3) on the preferred anchor side (V), uncapped oracle sample; the
+    plain count (no per-anchor output) gives the same total."""
+    g, h = large
+    total, side = _large_sampled(sbc, g, h, 3, 3, 333)
+    assert side == 1
+    assert total == sbc.sbc_count(h, 3, 3)
+
+
+def test_large_43_sampled_anchors(sbc, large):
+    """(4,3): four vertices from U, three from V; anchored on V, where the
+    tuples have three vertices (two partners: the tensor-core form)."""
+    g, h = large
+    _, side = _large_sampled(sbc, g, h, 4, 3, 433)
+    assert side == 1
+
+
+def test_large_34_sampled_anchors(sbc, large):
+    """(3,4): three vertices from U, four from V. The automatic side is U
+    (tuples of three there, of four on V); per-anchor values against the
+    oracle."""
+    g, h = large
+    _, side = _large_sampled(sbc, g, h, 3, 4, 344)
+    assert side == 0
