@@ -382,6 +382,30 @@ def serve_leg(sbc, torch, args):
             "rates": out}
 
 
+def pq_sweep_leg(sbc, torch, args):
+    """Seconds per exact count for p in {3,4,5}, q in {3..7} (the paper's
+    (p,q) experiments) on the 20k- and 2M-edge graphs: automatic anchor side,
+    graph resident, median of three counts."""
+    out = {}
+    for name in ("plain-2k-1.5k-20k", "plain-200k-100k-2M"):
+        g = load_workload(name)
+        rows = []
+        with sbc.graph_from_synth(g, device=True) as h:
+            for p in (3, 4, 5):
+                for q in range(3, 8):
+                    times, st = [], None
+                    for _ in range(3):
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        c, st, _ = sbc.sbc_count_ex(h, p, q)
+                        times.append(time.perf_counter() - t0)
+                    rows.append({"pq": f"({p},{q})", "count": c, "s": float(np.median(times)),
+                                 "side": "UV"[st["anchor_side"]],
+                                 "tc_anchors": st["tc_anchors"]})
+        out[name] = rows
+    return out
+
+
 def _leg(fn, *a):
     """Run an extra leg; a failure is reported in the leg's object (the main
     line is still printed) and on stderr."""
@@ -577,7 +601,9 @@ def run_ours(args):
                          f"{dt:.1f} s; graph lists built once beforehand)",
                "seconds_to_exact_33_estimate": dt / args.cpu_frac}
 
-    medium = batch = serve = None
+    medium = batch = serve = sweep = None
+    if rank == 0 and ws == 1 and args.pq_sweep:
+        sweep = _leg(pq_sweep_leg, sbc, torch, args)
     if rank == 0 and ws == 1 and not args.no_medium:
         medium = _leg(medium_leg, sbc, torch, args)
     if rank == 0 and ws == 1 and args.batch_graphs > 0:
@@ -608,6 +634,7 @@ def run_ours(args):
             "roofline": roof, "roofline_kernels": roofs, "peak_source": peak_kind,
             "alu_rates": alu, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
             "cpu_baseline": cpu, "medium": medium, "batch": batch, "serve": serve,
+            "pq_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -626,6 +653,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-medium", action="store_true", help="skip the 2M-edge leg")
+    ap.add_argument("--pq-sweep", action="store_true",
+                    help="also time p in {3,4,5} x q in {3..7} on the 20k- and 2M-edge graphs")
     ap.add_argument("--batch-graphs", type=int, default=10000,
                     help="graphs of the batch leg (0 skips it; the full recipe is 10000)")
     ap.add_argument("--serve-graphs", type=int, default=500)
@@ -637,7 +666,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.0,
                     help="arrival span per rate: requests = min(serve-requests, rate x this)")
     ap.add_argument("--serve-rates", type=float, nargs="+",
-                    default=[100.0, 1000.0, 5000.0, 20000.0])
+                    default=[50.0, 100.0, 150.0, 300.0, 1000.0, 5000.0, 20000.0])
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
     ap.add_argument("--serve-baseline-requests", type=int, default=2000,
                     help="requests (a prefix of each rate's arrivals) served one at a time")

@@ -151,7 +151,7 @@ sbc_status sbc_graph_info(const sbc_graph *g, sbc_graph_info_t *out);
  *                  step: the four type-class sizes of every candidate pair are
  *                  entries of a Gram matrix of the candidates' 0/1 masks,
  *                  computed by tcgen05 MMAs. -1 turns the step off, 1..65536
- *                  sets the threshold, default 5.
+ *                  sets the threshold, default 2.
  * SBC_E_INVAL for a field outside its range.
  */
 typedef struct {

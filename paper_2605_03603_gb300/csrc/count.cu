@@ -2461,7 +2461,7 @@ constexpr unsigned long long kPosNodeCost = 3;
 constexpr unsigned long long kSplitPerWarp = 4;
 // Two-partner anchors with at least this many mask words and candidates take
 // the tensor-core pair step.
-constexpr uint32_t kTcMinWords = 5;
+constexpr uint32_t kTcMinWords = 2;
 constexpr uint32_t kTcMinCandidates = 128;
 
 // Largest x with binom(x, l) computable in 64 bits by the multiplicative
@@ -2500,6 +2500,20 @@ void ensure_kernel_attrs() {
     SBC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) fail(SBC_E_UNSUPPORTED, "device ordinal %d out of range", dev);
     if (done[dev]) return;
+    // Counts allocate and free their buffers (plans, candidate pools, the
+    // tensor-core Z arena) on the stream from the device's default memory
+    // pool; let the pool keep up to 4 GiB of freed memory mapped between
+    // counts instead of returning it at every synchronisation.
+    {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = 4ull << 30, cur = 0;
+            if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess &&
+                cur < keep)
+                SBC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        }
+        cudaGetLastError();
+    }
     unsigned long long lim[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int i = 2; i <= 8; i++) lim[i] = binom64_limit(i);
     SBC_CUDA(cudaMemcpyToSymbol(c_binom64_max, lim, sizeof(lim)));
@@ -2614,7 +2628,7 @@ struct CountRun {
         size_t fr = 0, tot = 0;
         SBC_CUDA(cudaMemGetInfo(&fr, &tot));
         int64_t b = (int64_t)(fr / 8);
-        return std::max<int64_t>(256ll << 20, std::min<int64_t>(b, 8ll << 30));
+        return std::max<int64_t>(256ll << 20, std::min<int64_t>(b, 1ll << 30));
     }
 
     // Events around the 2-hop and tuple launches of each group (pairs).

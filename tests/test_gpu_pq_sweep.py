@@ -1,0 +1,75 @@
+"""The (p,q) sweep of the paper's experiments (p in {3,4,5}, q in {3..7}):
+every point on the 20k-edge graph against the oracle's whole count, and on
+the 2M-edge graph per anchor (a seeded sample including the heaviest
+anchors) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import sbc_synth
+
+pytestmark = pytest.mark.gpu
+
+SWEEP = [(p, q) for p in (3, 4, 5) for q in range(3, 8)]
+
+
+@pytest.fixture(scope="module")
+def sbc():
+    import torch
+
+    assert torch.cuda.is_available()
+    torch.cuda.init()
+    import paper_2605_03603_gb300 as m
+
+    return m
+
+
+def cheap_side(p, q):
+    """The oracle's faster side: the one with the smaller sets (their
+    depth-first extension goes min(p, q) levels deep)."""
+    return 0 if p <= q else 1
+
+
+@pytest.fixture(scope="module")
+def small(sbc):
+    g = sbc_synth.plain_small()
+    h = sbc.graph_from_synth(g)
+    yield g, h
+    h.close()
+
+
+@pytest.fixture(scope="module")
+def medium(sbc):
+    g = sbc_synth.plain_medium()
+    h = sbc.graph_from_synth(g, device=True)
+    yield g, h
+    h.close()
+
+
+@pytest.mark.parametrize("p,q", SWEEP)
+def test_sweep_small_equals_oracle(sbc, small, p, q):
+    g, h = small
+    want = oracle.count(g, p, q, side=cheap_side(p, q))
+    assert sbc.sbc_count(h, p, q) == want
+    other = 1 - cheap_side(p, q)
+    if max(p, q) <= 5:  # both anchor sides of the GPU path (tuples of at most 5)
+        assert sbc.sbc_count_ex(h, p, q, anchor_side=other)[0] == want
+
+
+@pytest.mark.parametrize("p,q", SWEEP)
+def test_sweep_medium_sampled_anchors(sbc, medium, p, q):
+    g, h = medium
+    total, st, per = sbc.sbc_count_ex(h, p, q, per_anchor=True)
+    side = st["anchor_side"]
+    assert sum(per) == total
+    perf = np.asarray([float(x) for x in per])
+    nz = np.nonzero(perf)[0]
+    rng = np.random.default_rng(1000 + 10 * p + q)
+    pick = set(rng.choice(len(per), size=20, replace=False).tolist())
+    if len(nz):
+        pick |= set(rng.choice(nz, size=min(16, len(nz)), replace=False).tolist())
+        pick |= set(nz[np.argsort(-perf[nz])][:4].tolist())
+    anchors = sorted(pick)
+    _, want = oracle.count(g, p, q, side=side, per_anchor=True, anchors=anchors)
+    mism = [(a, per[a], want[a]) for a in anchors if per[a] != want[a]]
+    assert not mism, mism[:5]
