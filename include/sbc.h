@@ -272,6 +272,21 @@ sbc_status sbc_autotune(const sbc_graph *const *graphs, size_t n, int p, int q, 
                         sbc_tune_t *out, void *stream);
 
 /*
+ * sbc_autotune with a per-GPU cache (no counterpart in the paper). The cache
+ * is a text file at cache_path, one line per tuning: a key made of the GPU's
+ * name and SM count, p, q, and the powers of two just above the batch's graph
+ * count and total edges, then the chosen parameters and their time. When the
+ * file holds the key, *out is read from it and *from_cache = 1 (no kernel
+ * runs); else the search of sbc_autotune runs, its result is appended to the
+ * file and *from_cache = 0. from_cache may be NULL. SBC_E_INVAL when the file
+ * cannot be written or holds invalid parameters for the key. Writers that
+ * share one file should not append at the same time.
+ */
+sbc_status sbc_autotune_cached(const sbc_graph *const *graphs, size_t n, int p, int q,
+                               int32_t reps, const char *cache_path, sbc_tune_t *out,
+                               int32_t *from_cache, void *stream);
+
+/*
  * Serving. A server answers count requests (graph, p, q) on resident graphs
  * as they arrive. A scheduler thread forms jobs for a set of device lanes
  * (one stream and worker thread each): requests on small graphs that wait

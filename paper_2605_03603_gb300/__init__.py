@@ -146,6 +146,9 @@ _declare("sbc_batch_create_ex", ctypes.c_int,
 _declare("sbc_autotune", ctypes.c_int,
          [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int32,
           ctypes.POINTER(Tune), _vp])
+_declare("sbc_autotune_cached", ctypes.c_int,
+         [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int32,
+          ctypes.c_char_p, ctypes.POINTER(Tune), ctypes.POINTER(ctypes.c_int32), _vp])
 _declare("sbc_batch_run", ctypes.c_int, [_vp, ctypes.POINTER(U128), _vp])
 _declare("sbc_batch_destroy", ctypes.c_int, [_vp])
 
@@ -405,15 +408,25 @@ def sbc_count_batch(graphs, p: int, q: int, stream=None) -> list:
     return [out[i].value() for i in range(len(graphs))]
 
 
-def sbc_autotune(graphs, p: int, q: int, reps: int = 0, stream=None) -> dict:
+def sbc_autotune(graphs, p: int, q: int, reps: int = 0, stream=None, cache: str | None = None) -> dict:
     """sbc_autotune: the fastest launch parameters for counting this batch of
     graphs (one graph is a batch of one); returns sbc_tune_t's fields as a
-    dict, with "ms" the time of one count under them."""
+    dict, with "ms" the time of one count under them. With `cache` (a file
+    path), sbc_autotune_cached: a tuning stored there for this GPU and kind
+    of batch is reused (the dict's "from_cache" says so), else the search
+    runs and its result is stored."""
     out = Tune()
     gl = list(graphs)
-    _check(lib.sbc_autotune(_handles(gl), len(gl), p, q, reps, ctypes.byref(out),
-                            _stream_ptr(stream)))
-    return out.as_dict()
+    if cache is None:
+        _check(lib.sbc_autotune(_handles(gl), len(gl), p, q, reps, ctypes.byref(out),
+                                _stream_ptr(stream)))
+        return out.as_dict()
+    hit = ctypes.c_int32(0)
+    _check(lib.sbc_autotune_cached(_handles(gl), len(gl), p, q, reps, str(cache).encode(),
+                                   ctypes.byref(out), ctypes.byref(hit), _stream_ptr(stream)))
+    d = out.as_dict()
+    d["from_cache"] = bool(hit.value)
+    return d
 
 
 class Batch:

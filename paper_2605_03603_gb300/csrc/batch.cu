@@ -17,6 +17,9 @@
 // A batch object keeps the planned counts; sbc_batch_run replays their
 // counting kernels from a CUDA graph captured at creation.
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
 #include <vector>
 
 #include "sbc_internal.cuh"
@@ -409,6 +412,84 @@ sbc_status sbc_autotune(const sbc_graph *const *graphs, size_t n, int p, int q, 
     SBC_BATCH_TRY
     if (!out) fail(SBC_E_INVAL, "out is NULL");
     autotune(graphs, n, p, q, reps, out, (cudaStream_t)stream);
+    SBC_BATCH_END
+}
+
+namespace sbc {
+namespace {
+
+// Cache key of a tuning: the GPU (name and SM count) and the shape of the
+// batch (p, q, and the powers of two just above its graph count and total
+// edges), so batches of the same kind on the same GPU share one entry.
+std::string tune_key(const sbc_graph *const *gs, size_t n, int p, int q) {
+    int dev = 0, sms = 0;
+    SBC_CUDA(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    SBC_CUDA(cudaGetDeviceProperties(&prop, dev));
+    SBC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    uint64_t edges = 0;
+    for (size_t i = 0; i < n; i++) edges += gs[i] ? (uint64_t)gs[i]->nnz : 0;
+    std::string name(prop.name);
+    for (char &c : name)
+        if (c == ' ' || c == '\t' || c == '|') c = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s|%d|%d,%d|g%d|e%d", name.c_str(), sms, p, q, bits_for(n),
+             bits_for(edges));
+    return buf;
+}
+
+// Looks `key` up in the cache file (one line per entry: key, then the four
+// launch parameters and the time); the last matching line wins.
+bool tune_lookup(const char *path, const std::string &key, sbc_tune_t *out) {
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[512], k[300];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        sbc_tune_t t{};
+        if (sscanf(line, "%299s %d %d %d %d %f", k, &t.small_wedges, &t.pos_node_cost,
+                   &t.split_per_warp, &t.tc_min_words, &t.ms) == 6 &&
+            key == k) {
+            *out = t;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void tune_store(const char *path, const std::string &key, const sbc_tune_t &t) {
+    FILE *f = fopen(path, "a");
+    if (!f) fail(SBC_E_INVAL, "cannot open the tuning cache %s for appending", path);
+    fprintf(f, "%s %d %d %d %d %.4f\n", key.c_str(), t.small_wedges, t.pos_node_cost,
+            t.split_per_warp, t.tc_min_words, t.ms);
+    fclose(f);
+}
+
+}  // namespace
+}  // namespace sbc
+
+sbc_status sbc_autotune_cached(const sbc_graph *const *graphs, size_t n, int p, int q,
+                               int32_t reps, const char *cache_path, sbc_tune_t *out,
+                               int32_t *from_cache, void *stream) {
+    SBC_BATCH_TRY
+    if (!out || !cache_path || !*cache_path) fail(SBC_E_INVAL, "out and cache_path are required");
+    if (n == 0 || !graphs) fail(SBC_E_INVAL, "autotune needs at least one graph");
+    for (size_t i = 0; i < n; i++)
+        if (!graphs[i]) fail(SBC_E_INVAL, "graph %zu is NULL", i);
+    if (p < 2 || q < 2 || p > 8 || q > 8) fail(SBC_E_INVAL, "p and q must be in [2, 8]");
+    const std::string key = tune_key(graphs, n, p, q);
+    if (from_cache) *from_cache = 0;
+    sbc_tune_t t{};
+    if (tune_lookup(cache_path, key, &t)) {
+        CountSpec chk;
+        apply_tune(chk, &t);  // the stored fields must be valid launch parameters
+        *out = t;
+        if (from_cache) *from_cache = 1;
+    } else {
+        autotune(graphs, n, p, q, reps, out, (cudaStream_t)stream);
+        tune_store(cache_path, key, *out);
+    }
     SBC_BATCH_END
 }
 

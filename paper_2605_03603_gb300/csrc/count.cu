@@ -2749,12 +2749,14 @@ struct CountRun {
         cudaEvent_t t4 = timing ? new_event(ev_tc) : nullptr;
         cudaEvent_t t5 = timing ? new_event(ev_tc) : nullptr;
         if (t4) SBC_CUDA(cudaEventRecord(t4, s));
+        NvtxRange nr("sbc/tc_pairs");
         launch_tc(grp);
         if (t5) SBC_CUDA(cudaEventRecord(t5, s));
     }
     uint64_t tc_anchors = 0, tc_tiles = 0, tc_kblocks = 0;
 
     void plan_and_run(EventTimer *tm) {
+        NvtxRange nr("sbc/count");
         const bool timing = tm != nullptr;
         const int B = 256;
         groups.clear();
@@ -2911,7 +2913,10 @@ struct CountRun {
             cudaEvent_t t1 = timing ? new_event(ev_twohop) : nullptr;
             zero_pool(gi);
             if (t0) SBC_CUDA(cudaEventRecord(t0, s));
-            launch_twohop((unsigned)a, (unsigned)b);
+            {
+                NvtxRange nr("sbc/twohop");
+                launch_twohop((unsigned)a, (unsigned)b);
+            }
             if (t1) SBC_CUDA(cudaEventRecord(t1, s));
             // tuple phase planning (needs the candidate counts)
             ia.begin = a;
@@ -2971,7 +2976,10 @@ struct CountRun {
             cudaEvent_t t2 = timing ? new_event(ev_tuples) : nullptr;
             cudaEvent_t t3 = timing ? new_event(ev_tuples) : nullptr;
             if (t2) SBC_CUDA(cudaEventRecord(t2, s));
-            launch_tuple_kernel();
+            {
+                NvtxRange nr("sbc/tuples");
+                launch_tuple_kernel();
+            }
             if (t3) SBC_CUDA(cudaEventRecord(t3, s));
             run_tc_timed(gi, timing);
             n_items += ng;
@@ -3166,6 +3174,7 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
     tm.mark(0, s);
     {
         std::lock_guard<std::mutex> lock(g->mu);
+        NvtxRange nr("sbc/orientation");
         build_orientation(g, side, s);
     }
     const Orient &o = g->side[side];

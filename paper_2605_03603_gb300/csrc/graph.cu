@@ -285,6 +285,7 @@ namespace sbc {
 // the cost model prefers (which also checks for duplicate edges).
 sbc_graph *create_graph(int64_t n_u, int64_t n_v, int64_t nnz, const void *row_offsets,
                         const int32_t *cols, const void *signs, uint32_t flags, cudaStream_t s) {
+    NvtxRange nr("sbc/create_graph");
     if (n_u < 0 || n_v < 0 || nnz < 0) fail(SBC_E_INVAL, "negative size");
     if (n_u >= (1ll << 31) - 1 || n_v >= (1ll << 31) - 1 || nnz >= (1ll << 31) - 1)
         fail(SBC_E_UNSUPPORTED, "sizes must be below 2^31 - 1");

@@ -15,6 +15,8 @@
 #include <stdexcept>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sbc.h"
 
 namespace sbc {
@@ -38,6 +40,15 @@ void set_last_error(const std::string &msg);
 
 // Check for a launch error right after a kernel launch.
 #define SBC_LAUNCHED() SBC_CUDA(cudaGetLastError())
+
+// A named NVTX range for the lifetime of the object (phases of a count on a
+// profiler's timeline; free when no profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---------------------------------------------------------------- memory
 

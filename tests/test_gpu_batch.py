@@ -199,3 +199,29 @@ def test_batch_recipe_all_graphs_plain_equals_batched(sbc):
         finally:
             for h in hs:
                 h.close()
+
+
+def test_autotune_cache_reuses_the_tuning(sbc, tmp_path):
+    """The per-GPU tuning cache: the first call searches and stores, the
+    second finds the same key and returns the stored parameters without
+    running; a batch planned with them counts exactly; another (p, q) is a
+    different key."""
+    gs = mixed_graphs(20, 21)
+    want = [oracle.count(g, 3, 3, side=0) for g in gs]
+    hs = [sbc.graph_from_synth(g) for g in gs]
+    path = tmp_path / "tune_cache.txt"
+    try:
+        t1 = sbc.sbc_autotune(hs, 3, 3, reps=1, cache=path)
+        assert t1["from_cache"] is False and path.exists()
+        t2 = sbc.sbc_autotune(hs, 3, 3, reps=1, cache=path)
+        assert t2["from_cache"] is True
+        for k in ("small_wedges", "pos_node_cost", "split_per_warp", "tc_min_words"):
+            assert t1[k] == t2[k]
+        with sbc.Batch(hs, 3, 3, tune=t2) as b:
+            assert b.run() == want
+        t3 = sbc.sbc_autotune(hs, 4, 3, reps=1, cache=path)
+        assert t3["from_cache"] is False
+        assert len(path.read_text().splitlines()) == 2
+    finally:
+        for h in hs:
+            h.close()
