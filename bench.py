@@ -59,7 +59,7 @@ WORKLOAD = "plain-5M-1M-60M"
 PQ = [(3, 3)]
 # DRAM bytes (read + write) per launch of a kernel on a workload, from one ncu
 # capture of the current kernels; None where not captured.
-TRAFFIC = {}
+TRAFFIC = {("k_twohop", "plain-5M-1M-60M"): 1_407_377_885_696}
 
 
 def _dist():
@@ -123,7 +123,8 @@ class ClockSampler:
 
 
 WORKLOADS = {"plain-200k-100k-2M": "plain_medium", "plain-50k-25k-500k": "plain_quarter",
-             "plain-2k-1.5k-20k": "plain_small", "plain-5M-1M-60M": "plain_large"}
+             "plain-2k-1.5k-20k": "plain_small", "plain-5M-1M-60M": "plain_large",
+             "dense-3000x400": "dense_factions"}
 
 
 def load_workload(name=None):
@@ -643,6 +644,29 @@ def run_ours(args):
     return 0
 
 
+def run_profile_target(args):
+    """Plain counts of the workload (no timing contract): the command the
+    ncu summaries under profiles/ were taken with. Prints each count's
+    statistics."""
+    import torch
+
+    import paper_2605_03603_gb300 as sbc
+
+    torch.cuda.set_device(0)
+    g = load_workload()
+    side = {"auto": -1, "U": 0, "V": 1}[args.side]
+    with sbc.graph_from_synth(g, device=True) as h:
+        for _ in range(args.steps):
+            for p, q in PQ:
+                c, st, _ = sbc.sbc_count_ex(h, p, q, anchor_side=side)
+                print(json.dumps({"workload": WORKLOAD, "pq": f"({p},{q})", "count": c,
+                                  **{k: st[k] for k in ("anchor_side", "ms_total", "ms_twohop",
+                                                        "ms_tuples", "ms_tc", "wedges",
+                                                        "popc_words", "tc_tiles",
+                                                        "tc_kblocks")}}), flush=True)
+    return 0
+
+
 def main():
     global PQ, WORKLOAD
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
@@ -679,12 +703,18 @@ def main():
                     help="anchor sample fraction for the oracle CPU baseline")
     ap.add_argument("--ref-frac", type=float, default=0.0001,
                     help="anchor sample fraction per step for --impl reference")
+    ap.add_argument("--profile-target", action="store_true",
+                    help="only run --steps plain counts of the workload (for ncu)")
+    ap.add_argument("--side", choices=["auto", "U", "V"], default="auto",
+                    help="anchor side of --profile-target counts")
     args = ap.parse_args()
     WORKLOAD = args.workload
     if args.pq:
         PQ = [tuple(int(x) for x in pq.split(",")) for pq in args.pq]
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_target:
+        return run_profile_target(args)
     return run_ours(args)
 
 

@@ -225,6 +225,23 @@ def plain_quarter(seed: int = 2) -> SignedBipartite:
                            p_plus=_PI_75, name="plain-50k-25k-500k")
 
 
+def dense_factions(m: int = 3000, n: int = 400, density: float = 0.45, seed: int = 5,
+                   flip: float = 0.05) -> SignedBipartite:
+    """Dense random bipartite graph (each pair an edge with probability
+    `density`) with planted two-faction signs, a fraction `flip` flipped:
+    anchors with thousands of candidates over a few hundred positions (the
+    tensor-core pair step's profiling case at the defaults)."""
+    r = uniform01(seed, 21, m * n)
+    f = uniform01(seed, 22, m * n)
+    lab = uniform01(seed, 23, m + n)
+    lu = np.where(lab[:m] < 0.5, -1, 1)
+    lv = np.where(lab[m:] < 0.5, -1, 1)
+    uu, vv = np.divmod(np.arange(m * n, dtype=np.int64), n)
+    keep = r < density
+    s = (lu[uu] * lv[vv] * np.where(f < flip, -1, 1)).astype(np.int8)
+    return from_edges(m, n, uu[keep], vv[keep], s[keep], f"dense-{m}x{n}")
+
+
 def plain_large(seed: int = 3) -> SignedBipartite:
     """5,000,000 x 1,000,000, 60,000,000 edges, exponents 2.4 (U) / 1.9 (V),
     V hubs capped at 50,000 expected degree; 4 planted factions, flip 0.2."""
