@@ -59,7 +59,7 @@ WORKLOAD = "plain-5M-1M-60M"
 PQ = [(3, 3)]
 # DRAM bytes (read + write) per launch of a kernel on a workload, from one ncu
 # capture of the current kernels; None where not captured.
-TRAFFIC = {("k_twohop", "plain-5M-1M-60M"): 1_407_377_885_696}
+TRAFFIC = {}
 
 
 def _dist():
@@ -559,7 +559,9 @@ def run_ours(args):
                          "bound": "hbm", "achieved": hop_gbs, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": hop_gbs / peaks["hbm_gbs"], "ms": t_hop,
                          "traffic": TRAFFIC.get(("k_twohop", WORKLOAD)),
-                         "bytes_per_step": int(hop_bytes)}
+                         "bytes_per_step": int(hop_bytes),
+                         "entries_read_per_wedge": (sum(s["twohop_reads"] for s in s_first)
+                                                    / max(1, sum(s["wedges"] for s in s_first)))}
     dominant = max(roofs, key=lambda k: roofs[k]["ms"])
     roof = dict(roofs[dominant])
     roof["share_of_step"] = roof["ms"] / float(np.mean(step_ms))

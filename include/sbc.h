@@ -203,6 +203,18 @@ typedef struct {
     uint64_t tc_tiles;      /* 128 x 256 Gram-matrix tiles it computed */
     uint64_t tc_kblocks;    /* K steps of 128 positions over those tiles: the step made
                                tc_kblocks x 128 x 256 x 128 multiply-adds */
+    /* CTA-wide 2-hop kernel (anchors with more than the warp tier's wedges), by
+     * strategy: [0] one hash window, [1] wedges bucketed once by hash class,
+     * [2] the 2-hop re-read once per hash class (fallback), [3] bucketed, then
+     * scattered a second time at exact class offsets (a class overflowed its
+     * capacity) */
+    uint64_t twohop_reads;      /* 2-hop entries it read, all passes */
+    uint64_t twohop_anchors[4]; /* its anchors per strategy */
+    float twohop_share[4];      /* share of its SM time per strategy */
+    float twohop_tail_ms;       /* last minus first finish of its CTAs (load imbalance) */
+    uint64_t pool_bytes;        /* candidate-mask pool: bytes reserved over all anchor groups */
+    uint64_t twohop_split_classes; /* hash classes whose distinct partners overflowed one
+                                      table and were hashed in sub-class windows */
 } sbc_count_stats;
 
 /*

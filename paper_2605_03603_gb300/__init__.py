@@ -97,7 +97,10 @@ class CountStats(ctypes.Structure):
                 ("ms_prepare", ctypes.c_float), ("ms_twohop", ctypes.c_float),
                 ("ms_tuples", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("ms_tc", ctypes.c_float), ("tc_anchors", ctypes.c_uint64),
-                ("tc_tiles", ctypes.c_uint64), ("tc_kblocks", ctypes.c_uint64)]
+                ("tc_tiles", ctypes.c_uint64), ("tc_kblocks", ctypes.c_uint64),
+                ("twohop_reads", ctypes.c_uint64), ("twohop_anchors", ctypes.c_uint64 * 4),
+                ("twohop_share", ctypes.c_float * 4), ("twohop_tail_ms", ctypes.c_float),
+                ("pool_bytes", ctypes.c_uint64), ("twohop_split_classes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {"count": self.count.value(), "anchor_tuples": self.anchor_tuples.value(),
@@ -109,7 +112,11 @@ class CountStats(ctypes.Structure):
                 "ms_twohop": float(self.ms_twohop), "ms_tuples": float(self.ms_tuples),
                 "ms_total": float(self.ms_total), "ms_tc": float(self.ms_tc),
                 "tc_anchors": int(self.tc_anchors), "tc_tiles": int(self.tc_tiles),
-                "tc_kblocks": int(self.tc_kblocks)}
+                "tc_kblocks": int(self.tc_kblocks), "twohop_reads": int(self.twohop_reads),
+                "twohop_anchors": [int(x) for x in self.twohop_anchors],
+                "twohop_share": [round(float(x), 4) for x in self.twohop_share],
+                "twohop_tail_ms": float(self.twohop_tail_ms), "pool_bytes": int(self.pool_bytes),
+                "twohop_split_classes": int(self.twohop_split_classes)}
 
 
 _vp = ctypes.c_void_p

@@ -60,6 +60,13 @@ struct Counters {
     unsigned long long tested;         // tuples whose common-neighbour mask was tested
     unsigned long long leaves;         // tuples with |T| >= l (type counts taken)
     unsigned long long popc_words;     // mask words popcounted: W per test, 2^R W per leaf
+    // CTA-wide 2-hop kernel, by strategy (one window, bucketed, re-read windows,
+    // bucketed with a second scatter)
+    unsigned long long tw_reads;       // 2-hop entries read, all passes
+    unsigned long long tw_cyc[4];      // SM cycles spent on its anchors
+    unsigned long long tw_anchors[4];
+    unsigned long long tw_fin_max, tw_fin_min_n;  // CTA finish times (global ns; min kept as ~t)
+    unsigned long long tw_split;       // hash classes hashed in sub-class windows
     unsigned int head_large;           // 2-hop queue heads
     unsigned int head_small;
     unsigned int head_b;               // tuple queue head
@@ -250,8 +257,16 @@ constexpr uint32_t NOBIT = 0x7FFFFFFFu;
 __device__ __forceinline__ uint32_t hash_slot(uint32_t w, uint32_t hs) {
     return __umulhi(w * 0x9E3779B1u, hs);
 }
+__device__ __forceinline__ uint32_t class_mix(uint32_t w) {
+    return ((w * 0x85EBCA6Bu) ^ (w >> 15)) * 0xC2B2AE35u;
+}
+// Hash class of w among 2^lg (the top lg bits of its mix) ...
 __device__ __forceinline__ uint32_t class_of(uint32_t w, int lg) {
-    return lg ? (((w * 0x85EBCA6Bu) ^ (w >> 15)) * 0xC2B2AE35u) >> (32 - lg) : 0u;
+    return lg ? class_mix(w) >> (32 - lg) : 0u;
+}
+// ... and its sub-class among 2^lg2 within that class (the next lg2 bits).
+__device__ __forceinline__ uint32_t subclass_of(uint32_t w, int lg, int lg2) {
+    return lg2 ? (class_mix(w) << lg) >> (32 - lg2) : 0u;
 }
 
 // Add `add` to w's counters (open addressing, linear probing, at most hs
@@ -345,6 +360,7 @@ struct TwohopArgs {
     int l;
     int check;                      // run the candidate-mask self-check
     uint32_t hs_cap;                // test override: most hash slots per table (0: none)
+    uint32_t wcap;                  // most visited wedges of a one-window anchor
 };
 
 // Table size after the test override (which makes tables overflow on purpose,
@@ -534,6 +550,11 @@ constexpr size_t PL_SMEM = PL_OFF_STAGE + (size_t)PL_STAGE_WORDS * 4;
 // position (bits 32..52; all ones when the position is not useful).
 constexpr unsigned long long BE_NOBIT = (1ull << 21) - 1;
 
+__device__ __forceinline__ unsigned long long bucket_entry(uint32_t w, uint32_t sdiff, uint32_t bit) {
+    const unsigned long long bi = bit == EMPTY ? BE_NOBIT : (unsigned long long)bit;
+    return (unsigned long long)w | ((unsigned long long)sdiff << 31) | (bi << 32);
+}
+
 __host__ __device__ __forceinline__ unsigned long long bucket_cap(unsigned long long e_vis, int lg) {
     return ((e_vis >> lg) * 3) / 2 + 65;
 }
@@ -638,6 +659,12 @@ __device__ __forceinline__ void visit_block(int64_t ebase, int d, bool useful_on
     }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <bool STATS>
 __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -702,6 +729,10 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
         const uint32_t rsv = a.rsv_c[r];
         uint32_t *region = a.pool + a.pool_off[r];
         const unsigned long long e_vis = STATS ? a.e_all[r] : a.e_use[r];
+        const unsigned long long e_use = a.e_use[r];
+        const long long c0 = clock64();
+        unsigned long long reads = 0;
+        int path = 0;
         uint32_t nc = 0, npaper = 0;
         bool failed = false;
 
@@ -768,12 +799,13 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
 
         const int lgb = bucket_lg(e_vis);
         bool bucketed = false;
-        if (e_vis <= (unsigned long long)PL_WCAP) {
+        if (e_vis <= (unsigned long long)a.wcap) {
             // one window
             uint32_t hs = (uint32_t)((2 * e_vis + 31) & ~31ull);
             hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
             hs = cap_slots(hs, a);
             clear_table(hs);
+            reads = e_vis + e_use;
             visit_block(ebase, d, !STATS, 0, 0, a, pst, ppre, pinfo, warp_tot, &s_total,
                         [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
                             if (!tab_insert(keys, vals, hs, w, pass1_add(sdiff, bit))) s_ovf = 1;
@@ -802,59 +834,100 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
                         [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
                             uint32_t c = class_of(w, lgb);
                             uint32_t pos = atomicAdd(&s_bcnt[c], 1u);
-                            if (pos < cap) {
-                                unsigned long long bi = bit == EMPTY ? BE_NOBIT : (unsigned long long)bit;
-                                bucket[(size_t)c * cap + pos] =
-                                    (unsigned long long)w | ((unsigned long long)sdiff << 31) | (bi << 32);
-                            } else {
-                                s_ovf = 1;
-                            }
+                            if (pos < cap) bucket[(size_t)c * cap + pos] = bucket_entry(w, sdiff, bit);
+                            else s_ovf = 1;
                         });
-            bucketed = !s_ovf;
+            reads = e_vis;
+            path = 1;
             __syncthreads();
-            if (bucketed) {
-                for (uint32_t c = 0; c < ncls && !failed; c++) {
-                    const uint32_t n = s_bcnt[c];
-                    const unsigned long long *bk = bucket + (size_t)c * cap;
-                    uint32_t hs = (uint32_t)((2ull * n + 31) & ~31ull);
-                    hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
-                    hs = cap_slots(hs, a);
-                    __syncthreads();
-                    clear_table(hs);
-                    for (uint32_t i = tid; i < n; i += PL_THREADS) {
-                        unsigned long long e = bk[i];
-                        uint32_t bi = (uint32_t)(e >> 32);
-                        uint32_t bit = bi == (uint32_t)BE_NOBIT ? EMPTY : bi;
-                        if (!tab_insert(keys, vals, hs, (uint32_t)e & VMASK,
-                                        pass1_add((uint32_t)(e >> 31) & 1u, bit)))
-                            s_ovf = 1;
-                    }
-                    __syncthreads();
-                    if (s_ovf) {
-                        failed = true;
+            // A partner sharing many of the anchor's positions fills its class
+            // beyond the capacity. The class sizes are exact all the same, so
+            // the wedges are then scattered once more, classes back to back.
+            const bool packed = s_ovf != 0;
+            if (packed) {
+                uint32_t *cursor = keys;  // the table is free until the windows
+                const uint32_t c2 = 2 * tid;
+                const uint32_t n0 = c2 < ncls ? s_bcnt[c2] : 0u;
+                const uint32_t n1 = c2 + 1 < ncls ? s_bcnt[c2 + 1] : 0u;
+                const unsigned long long ex = block_excl_scan_u64(n0 + n1, warp_tot, &s_total);
+                if (c2 < ncls) cursor[c2] = (uint32_t)ex;
+                if (c2 + 1 < ncls) cursor[c2 + 1] = (uint32_t)ex + n0;
+                __syncthreads();
+                visit_block(ebase, d, !STATS, 0, 0, a, pst, ppre, pinfo, warp_tot, &s_total,
+                            [&](uint32_t w, uint32_t sdiff, uint32_t bit) {
+                                uint32_t pos = atomicAdd(&cursor[class_of(w, lgb)], 1u);
+                                bucket[pos] = bucket_entry(w, sdiff, bit);
+                            });
+                reads += e_vis;
+                path = 3;
+                __syncthreads();
+            }
+            bucketed = true;
+            size_t base = 0;
+            for (uint32_t c = 0; c < ncls && !failed; c++) {
+                const uint32_t n = s_bcnt[c];
+                const unsigned long long *bk = bucket + (packed ? base : (size_t)c * cap);
+                base += n;
+                if (n == 0) continue;
+                // one window for the class; when its distinct partners overflow
+                // the table, 2^lg2 windows over its sub-classes
+                const uint32_t nc0 = nc, np0 = npaper;
+                for (int lg2 = 0; !failed; lg2++) {
+                    if (lg2 > 8) {
                         if (tid == 0) atomicOr(&a.cnt->err, CERR_HASH);
+                        failed = true;
                         break;
                     }
-                    failed = !finish_window(hs, [&](uint32_t *bb, uint32_t bstride) {
+                    const uint32_t per = (n + (1u << lg2) - 1) >> lg2;
+                    uint32_t hs = (uint32_t)((2ull * per + 31) & ~31ull);
+                    hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
+                    hs = cap_slots(hs, a);
+                    nc = nc0;
+                    npaper = np0;
+                    bool over = false;
+                    for (uint32_t sub = 0; sub < (1u << lg2) && !failed; sub++) {
+                        __syncthreads();
+                        clear_table(hs);
                         for (uint32_t i = tid; i < n; i += PL_THREADS) {
                             unsigned long long e = bk[i];
+                            const uint32_t w = (uint32_t)e & VMASK;
+                            if (lg2 && subclass_of(w, lgb, lg2) != sub) continue;
                             uint32_t bi = (uint32_t)(e >> 32);
-                            if (bi == (uint32_t)BE_NOBIT) continue;
-                            set_bits(hs, bb, bstride, W, (uint32_t)e & VMASK,
-                                     (uint32_t)(e >> 31) & 1u, bi);
+                            uint32_t bit = bi == (uint32_t)BE_NOBIT ? EMPTY : bi;
+                            if (!tab_insert(keys, vals, hs, w, pass1_add((uint32_t)(e >> 31) & 1u, bit)))
+                                s_ovf = 1;
                         }
-                    });
+                        __syncthreads();
+                        if (s_ovf) {
+                            over = true;
+                            break;
+                        }
+                        failed = !finish_window(hs, [&](uint32_t *bb, uint32_t bstride) {
+                            for (uint32_t i = tid; i < n; i += PL_THREADS) {
+                                unsigned long long e = bk[i];
+                                uint32_t bi = (uint32_t)(e >> 32);
+                                if (bi == (uint32_t)BE_NOBIT) continue;
+                                const uint32_t w = (uint32_t)e & VMASK;
+                                if (lg2 && subclass_of(w, lgb, lg2) != sub) continue;
+                                set_bits(hs, bb, bstride, W, w, (uint32_t)(e >> 31) & 1u, bi);
+                            }
+                        });
+                    }
+                    if (!over) break;
+                    if (lg2 == 0 && tid == 0) atomicAdd(&a.cnt->tw_split, 1ull);
                 }
             }
         }
-        if (!bucketed && !failed && e_vis > (unsigned long long)PL_WCAP) {
+        if (!bucketed && !failed && e_vis > (unsigned long long)a.wcap) {
             // re-read windows: every pass over the 2-hop keeps one hash class
             nc = 0;
             npaper = 0;
             int lg_nw = 0;
-            while (((unsigned long long)PL_WCAP << lg_nw) < e_vis) lg_nw++;
+            while (((unsigned long long)a.wcap << lg_nw) < e_vis) lg_nw++;
+            path = 2;
             for (int attempt = 0; attempt < 8 && !failed; attempt++) {
                 const uint32_t nw = 1u << lg_nw;
+                reads += (unsigned long long)nw * (e_vis + e_use);
                 const unsigned long long per = (e_vis + nw - 1) >> lg_nw;
                 uint32_t hs = (uint32_t)((2 * per + 31) & ~31ull);
                 hs = hs < 64 ? 64 : (hs > PL_HS ? PL_HS : hs);
@@ -894,10 +967,18 @@ __global__ void __launch_bounds__(PL_THREADS) k_twohop_large(TwohopArgs a) {
             a.ncand[r] = nc;
             if (STATS) a.npaper[r] = npaper;
             wedges += e_vis;
+            atomicAdd(&a.cnt->tw_reads, reads);
+            atomicAdd(&a.cnt->tw_cyc[path], (unsigned long long)(clock64() - c0));
+            atomicAdd(&a.cnt->tw_anchors[path], 1ull);
         }
         __syncthreads();
     }
-    if (tid == 0 && wedges) atomicAdd(&a.cnt->wedges, wedges);
+    if (tid == 0) {
+        if (wedges) atomicAdd(&a.cnt->wedges, wedges);
+        const unsigned long long t = global_ns();
+        atomicMax(&a.cnt->tw_fin_max, t);
+        atomicMax(&a.cnt->tw_fin_min_n, ~t);
+    }
 }
 
 // ------------------------------------------------------------------ groups
@@ -2718,6 +2799,12 @@ struct CountRun {
 
     std::vector<std::pair<int64_t, int64_t>> groups;  // ranges of the sorted anchors
     std::vector<int64_t> cum;  // pool words before each sorted anchor
+    float tw_tail_ms = 0;      // largest finish spread of the CTA-wide 2-hop kernel's CTAs
+
+    // Finish spread of the CTA-wide 2-hop launch of the last group (counters in hc).
+    float group_tail_ms() const {
+        return hc.tw_fin_max ? (float)((double)(hc.tw_fin_max - ~hc.tw_fin_min_n) * 1e-6) : 0.f;
+    }
     float ms_twohop = 0, ms_tuples = 0, ms_tc = 0;
     std::vector<cudaEvent_t> ev_tc;
 
@@ -2840,13 +2927,14 @@ struct CountRun {
         ta.l = l;
         ta.check = spec.check ? 1 : 0;
         ta.hs_cap = hash_slots_cap();
+        ta.wcap = twohop_window_wedges();
         ta.bucket = nullptr;
         ta.bucket_slot = 0;
         if (hc.n_big > 0) {
             const void *fn = spec.paper ? (const void *)k_twohop_large<true> : (const void *)k_twohop_large<false>;
             ga = sms * blocks_per_sm(fn, PL_THREADS, PL_SMEM);
             if ((int64_t)ga > (int64_t)hc.n_big) ga = (int)hc.n_big;
-            if (hc.e_max > (unsigned long long)PL_WCAP) {
+            if (hc.e_max > (unsigned long long)ta.wcap) {
                 const int lgb = bucket_lg(hc.e_max);
                 ta.bucket_slot = bucket_cap(hc.e_max, lgb) << lgb;
                 bucket.alloc((size_t)ga * ta.bucket_slot, s);
@@ -2909,6 +2997,7 @@ struct CountRun {
             SBC_CUDA(cudaMemsetAsync(&cnt.ptr->head_large, 0, 3 * sizeof(unsigned), s));
             SBC_CUDA(cudaMemsetAsync(&cnt.ptr->cost_total, 0, sizeof(unsigned long long), s));
             SBC_CUDA(cudaMemsetAsync(&cnt.ptr->n_tc, 0, sizeof(unsigned), s));
+            SBC_CUDA(cudaMemsetAsync(&cnt.ptr->tw_fin_max, 0, 2 * sizeof(unsigned long long), s));
             cudaEvent_t t0 = timing ? new_event(ev_twohop) : nullptr;
             cudaEvent_t t1 = timing ? new_event(ev_twohop) : nullptr;
             zero_pool(gi);
@@ -2931,6 +3020,7 @@ struct CountRun {
             g_launches++;
             SBC_CUDA(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
             SBC_CUDA(cudaStreamSynchronize(s));
+            tw_tail_ms = std::max(tw_tail_ms, group_tail_ms());
             if (hc.n_tc > 0) plan_tc(gi, hc.n_tc);
             const unsigned long long spw =
                 spec.split_per_warp > 0 ? (unsigned long long)spec.split_per_warp : kSplitPerWarp;
@@ -3028,6 +3118,15 @@ struct CountRun {
         res.tc_anchors = tc_anchors;
         res.tc_tiles = tc_tiles;
         res.tc_kblocks = tc_kblocks;
+        res.twohop_reads = hc.tw_reads;
+        res.twohop_split = hc.tw_split;
+        const double cyc = (double)(hc.tw_cyc[0] + hc.tw_cyc[1] + hc.tw_cyc[2] + hc.tw_cyc[3]);
+        for (int i = 0; i < 4; i++) {
+            res.twohop_anchors[i] = hc.tw_anchors[i];
+            res.twohop_share[i] = cyc > 0 ? (float)(hc.tw_cyc[i] / cyc) : 0.f;
+        }
+        res.twohop_tail_ms = std::max(tw_tail_ms, group_tail_ms());
+        res.pool_bytes = cum.empty() ? 0 : (uint64_t)cum.back() * 4;
     }
 };
 
@@ -3110,6 +3209,16 @@ uint32_t hash_slots_cap() {
     if (v <= 0) return 0;
     if (v > (1 << 20)) v = 1 << 20;
     v &= ~31ll;
+    return (uint32_t)(v < 32 ? 32 : v);
+}
+
+// Visited wedges up to which the CTA-wide 2-hop kernel hashes an anchor in one
+// window (above: bucketed by hash class). SBC_TWOHOP_WINDOW (tests only)
+// lowers it, from 32 up, so that small graphs take the bucketed strategy.
+uint32_t twohop_window_wedges() {
+    const char *e = getenv("SBC_TWOHOP_WINDOW");
+    long long v = e && *e ? atoll(e) : 0;
+    if (v <= 0 || v > PL_WCAP) return (uint32_t)PL_WCAP;
     return (uint32_t)(v < 32 ? 32 : v);
 }
 
@@ -3203,6 +3312,14 @@ void count_graph(const sbc_graph *gc, int p, int q, const sbc_count_opts *opts,
         stats->tc_anchors = res.tc_anchors;
         stats->tc_tiles = res.tc_tiles;
         stats->tc_kblocks = res.tc_kblocks;
+        stats->twohop_reads = res.twohop_reads;
+        stats->twohop_split_classes = res.twohop_split;
+        for (int i = 0; i < 4; i++) {
+            stats->twohop_anchors[i] = res.twohop_anchors[i];
+            stats->twohop_share[i] = res.twohop_share[i];
+        }
+        stats->twohop_tail_ms = res.twohop_tail_ms;
+        stats->pool_bytes = res.pool_bytes;
         stats->kernels = (int32_t)(g_launches.load() - kernels0);
         if (tm.on) {
             stats->ms_total = tm.ms(0, 4);

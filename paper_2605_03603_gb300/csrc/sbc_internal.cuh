@@ -219,6 +219,8 @@ struct CountResult {
     sbc_u128 count{0, 0}, anchor_tuples{0, 0};
     uint64_t candidates = 0, wedges = 0, work_items = 0, tested = 0, typed = 0, popc_words = 0;
     uint64_t tc_anchors = 0, tc_tiles = 0, tc_kblocks = 0;
+    uint64_t twohop_reads = 0, twohop_anchors[4] = {0, 0, 0, 0}, pool_bytes = 0, twohop_split = 0;
+    float twohop_share[4] = {0, 0, 0, 0}, twohop_tail_ms = 0;
 };
 struct CountRun;
 struct EventTimer;
@@ -248,6 +250,9 @@ bool debug_checks_env();
 uint32_t tc_min_candidates();
 // SBC_HASH_SLOTS_CAP (tests only): the 2-hop tables' slot cap, 0 for none.
 uint32_t hash_slots_cap();
+// SBC_TWOHOP_WINDOW (tests only): wedges of a one-window anchor of the CTA-wide
+// 2-hop kernel (default and largest: its table's half).
+uint32_t twohop_window_wedges();
 // Applies launch parameters (NULL or zero fields: defaults) to a count spec;
 // SBC_E_INVAL when a field is out of range.
 void apply_tune(CountSpec &spec, const sbc_tune_t *t);
