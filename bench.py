@@ -124,7 +124,7 @@ class ClockSampler:
 
 WORKLOADS = {"plain-200k-100k-2M": "plain_medium", "plain-50k-25k-500k": "plain_quarter",
              "plain-2k-1.5k-20k": "plain_small", "plain-5M-1M-60M": "plain_large",
-             "dense-3000x400": "dense_factions"}
+             "dense-3000x400": "dense_factions", "dense-3000x800": "dense_factions_wide"}
 
 
 def load_workload(name=None):

@@ -22,10 +22,11 @@
 //   G (only tiles that hold a pair a < b in candidate order). Per CTA: one
 //   producer warp issues the bulk copies into a 4-stage ring, one warp issues
 //   tcgen05.mma (kind::f8f6f4, M = 128, N = 256, K = 32 per instruction)
-//   into one of two TMEM accumulators, and four epilogue warps read the
+//   into one of two TMEM accumulators, and eight epilogue warps read the
 //   accumulator with tcgen05.ld, convert each entry to an integer, and add
-//   binom(G[a][b], l) (a shared table up to 256, exact 128-bit arithmetic
-//   above). The fp32 accumulator holds these integer sums exactly (each is
+//   binom(G[a][b], l) (32-bit table lookups when the anchor's positions
+//   bound every entry, else a 64-bit table up to 256 and exact 128-bit
+//   arithmetic above). The fp32 accumulator holds these integer sums exactly (each is
 //   at most d' < 2^21 < 2^24).
 //
 // Every wait on an mbarrier is bounded by a clock limit; a wait that runs out
@@ -275,6 +276,21 @@ __device__ __forceinline__ unsigned long long binom_u64c(unsigned long long x) {
     return r;
 }
 
+// Largest multiple of 32 (at most 2048) with 32 * binom(x, L) < 2^32: for
+// anchors of at most this many useful positions every Gram entry indexes a
+// 32-bit table and 32 of its binomials sum in 32 bits.
+template <int L>
+__host__ __device__ constexpr uint32_t tc_fast_max() {
+    uint32_t best = 0;
+    for (uint32_t x = 32; x <= 2048; x += 32) {
+        unsigned long long b = 1;
+        for (int i = 1; i <= L; i++) b = b * (x - L + i) / i;
+        if (32ull * b >= (1ull << 32)) break;
+        best = x;
+    }
+    return best;
+}
+
 template <int L>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tcpairs(TcArgs a) {
     extern __shared__ __align__(16) unsigned char tc_smem_raw[];
@@ -285,11 +301,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tcpairs(TcArgs a) {
     // binom(x, L) for x <= TC_BINOM, zero below L and at TC_BINOM + 1 (the
     // clamped index of larger entries, which a slower path adds)
     __shared__ unsigned long long s_bt[TC_BINOM + 2];
+    // binom(x, L) for x <= FAST in 32 bits (anchors with 32 W <= FAST)
+    constexpr uint32_t FAST = tc_fast_max<L>();
+    __shared__ uint32_t s_bt32[FAST + 1];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char *smem =
         (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
     for (int x = tid; x <= TC_BINOM + 1; x += TC_THREADS)
         s_bt[x] = (x >= L && x <= TC_BINOM) ? binom_u64c<L>(x) : 0ull;
+    for (int x = tid; x <= (int)FAST; x += TC_THREADS)
+        s_bt32[x] = x >= L ? (uint32_t)binom_u64c<L>(x) : 0u;
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; s++) {
             mbar_init(&full[s], 1);
@@ -445,10 +466,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tcpairs(TcArgs a) {
             // all of them off the diagonal, from c0 on it
             const uint32_t c0 = ca + 1 > tr.J * 128 ? (ca + 1 - tr.J * 128) * 2 : 0u;
             const uint32_t cl0 = __shfl_sync(0xffffffffu, c0, 0);  // smallest in the warp
+            // entries are at most the anchor's useful positions (<= 32 W)
+            const bool fast = 32ull * tr.A.W <= FAST;
             for (uint32_t cb = half * 128; cb < half * 128 + 128; cb += 32) {
                 if (cb + 32 <= cl0) continue;  // no lane keeps a column here (warp-uniform)
                 uint32_t v[32];
                 tmem_ld32(tmem + ((g * 32) << 16) + buf * 256 + cb, v);
+                if (fast && cb >= c0) {
+                    // The float bits of entry + 2^23 are 0x4B000000 + entry;
+                    // the table's address is offset by that constant (32-bit
+                    // shared-window arithmetic), and the bits are clamped to
+                    // the table's end.
+                    const uint32_t tb = smem_u32(s_bt32) - (0x4B000000u << 2);
+                    uint32_t part32 = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const uint32_t bits =
+                            min(__float_as_uint(__uint_as_float(v[j]) + 8388608.0f), 0x4B000000u + FAST);
+                        uint32_t b;
+                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(b) : "r"(tb + (bits << 2)));
+                        part32 += b;
+                    }
+                    sum.add((unsigned long long)part32);
+                    continue;
+                }
                 unsigned long long part = 0;  // < 32 * binom(256, 8) < 2^64
                 uint32_t mx = 0;
                 if (cb >= c0) {

@@ -299,3 +299,10 @@ def batch_graphs(seed: int, count: int, m_lo: float = 500, m_hi: float = 500_000
     threads = threads or min(32, os.cpu_count() or 1)
     with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
         return list(ex.map(lambda i: batch_graph(seed, i, m_lo, m_hi), range(start, start + count)))
+
+
+def dense_factions_wide() -> SignedBipartite:
+    """dense_factions over 800 positions: anchors of about 360 useful
+    positions (three 128-position blocks), the typical tensor-core tile of
+    the 60M-edge graph's (3,3) count."""
+    return dense_factions(n=800, seed=6)
