@@ -57,9 +57,11 @@ sys.path.insert(0, ROOT)
 METRIC = "anchor tuples/sec and seconds to exact balanced (3,3) count; batched graphs/sec, p99"
 WORKLOAD = "plain-5M-1M-60M"
 PQ = [(3, 3)]
-# DRAM bytes (read + write) per launch of a kernel on a workload, from one ncu
-# capture of the current kernels; None where not captured.
-TRAFFIC = {}
+# DRAM bytes (read + write) of a kernel's launches in one step of a workload
+# (the same unit as the kernel's `achieved`), from one ncu capture of the
+# current kernels; None where not captured. k_twohop: its two CTA-tier
+# launches of the (3,3) count.
+TRAFFIC = {("k_twohop", "plain-5M-1M-60M"): 279_530_419_712}
 
 
 def _dist():
