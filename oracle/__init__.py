@@ -17,6 +17,11 @@ Independent counters:
   V, kept when L x R is complete and every butterfly in it has an even number
   of negative edges. Graphs of at most 64 vertices per side.
 * `brute_count` -- the same definition in pure Python, for the tiniest cases.
+* `bbwc_count` -- the wedge-centric method (BBWC, Algorithm 1, Section 4.2)
+  in plain C (`sbc_bbwc.c`, its own library sharing no code with
+  `sbc_oracle.c`): signed p-wedges of each anchor bucketed by type and
+  anchor set, binom(wedges, q) per bucket. A second cross-check of `count`
+  on graphs too large for brute force.
 
 Convention (the problem statement takes p vertices from one partition and q
 from the other): p vertices come from U (the CSR rows) and q from V.
@@ -35,19 +40,28 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sbc_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libsbc_oracle.so")
+_BBWC_SRC = os.path.join(_HERE, "sbc_bbwc.c")
+_BBWC_PATH = os.path.join(_BUILD, "libsbc_bbwc.so")
 _lib = None
+_bbwc = None
+
+
+def _compile(src: str, lib: str, force: bool) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-fopenmp", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, src]
+        )
+        os.replace(tmp, lib)
+    return lib
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle (gcc -O2 -fopenmp) into oracle/_build/."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-fopenmp", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC]
-        )
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    """Compile the C oracle and the wedge-centric cross-check (gcc -O2
+    -fopenmp) into oracle/_build/; returns the oracle's library path."""
+    _compile(_BBWC_SRC, _BBWC_PATH, force)
+    return _compile(_SRC, _LIB_PATH, force)
 
 
 def _declare(lib):
@@ -95,6 +109,39 @@ def _load():
     if _lib is None:
         _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def _load_bbwc():
+    global _bbwc
+    if _bbwc is None:
+        build()
+        lib = ctypes.CDLL(_BBWC_PATH)
+        lib.sbc_bbwc_count.restype = ctypes.c_int
+        lib.sbc_bbwc_count.argtypes = [
+            ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.POINTER(ctypes.c_uint64)]
+        _bbwc = lib
+    return _bbwc
+
+
+def bbwc_count(g, p: int, q: int, side: int | None = None, threads: int = 0) -> int:
+    """Balanced (p,q)-bicliques of `g` (p from U, q from V) by the
+    wedge-centric method of Algorithm 1 (Section 4.2), on anchor side `side`
+    (0 = U, 1 = V; default the smaller partition). Independent of `count`."""
+    if side is None:
+        side = default_side(g.n_u, g.n_v)
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    col = np.ascontiguousarray(g.cols, dtype=np.int32)
+    sgn = np.ascontiguousarray(g.signs, dtype=np.int8)
+    out = (ctypes.c_uint64 * 2)()
+    rc = _load_bbwc().sbc_bbwc_count(g.n_u, g.n_v, off.ctypes.data, col.ctypes.data,
+                                     sgn.ctypes.data, p, q, side, threads, out)
+    if rc == 1:
+        raise OverflowError("balanced biclique count exceeds 128 bits")
+    if rc != 0:
+        raise RuntimeError(f"wedge-centric count failed with code {rc}")
+    return _u128(out[0], out[1])
 
 
 def max_threads() -> int:
