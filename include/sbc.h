@@ -379,6 +379,49 @@ sbc_status sbc_count_csr_noalloc(int64_t n_u, int64_t n_v, int64_t nnz, const vo
 sbc_status sbc_measure_alu_rates(double *popc_per_s, double *lop3_per_s, void *stream);
 
 /* Human-readable message for the last non-OK status on this thread. */
+/*
+ * Dynamic graphs (the setting the paper leaves to future work, Section 6): a
+ * balanced (p,q) count kept exact while edges are inserted, deleted or change
+ * sign. An update of edge (u, v) changes the count by the balanced bicliques
+ * that contain it; these are the complete (p-1, q-1) subgraphs of the local
+ * graph H(u, v) on Gamma(v) - {u} (rows) and Gamma(u) - {v} (columns) whose
+ * edges are the (w, x) with sign(u,v) sign(u,x) sign(w,v) sign(w,x) = +1 (a
+ * biclique through (u, v) is balanced exactly when its butterflies through
+ * (u, v) are). H is assembled on the host from the handle's adjacency (kept
+ * there, sorted per vertex) and counted by the GPU kernels (its balanced
+ * (p-1, q-1) count with every sign positive); p and q are in [3, 8].
+ */
+typedef struct sbc_dyn sbc_dyn; /* opaque, owned by the caller */
+#define SBC_DYN_INSERT 0   /* add edge (u, v) with `sign`; the edge must be absent */
+#define SBC_DYN_DELETE 1   /* remove edge (u, v); it must be present (`sign` unused) */
+#define SBC_DYN_SET_SIGN 2 /* give the present edge (u, v) the sign `sign` */
+
+/* Start from a host CSR over U (int64 offsets, int32 columns, int8 signs +1 /
+ * -1; validated like sbc_graph_create) and count it on the GPU. SBC_E_INVAL
+ * when p or q is outside [3, 8]. */
+sbc_status sbc_dyn_create(sbc_dyn **out, int64_t n_u, int64_t n_v, int64_t nnz,
+                          const int64_t *row_offsets, const int32_t *cols, const int8_t *signs,
+                          int p, int q, void *stream);
+/* Apply one update and write the new count to *count (host, may be NULL).
+ * SBC_E_INVAL for an absent edge (delete, set sign), a present one (insert), a
+ * vertex outside the graph or a sign other than +1 / -1; the handle is
+ * unchanged on any error. */
+sbc_status sbc_dyn_update(sbc_dyn *d, int op, int64_t u, int64_t v, int8_t sign, sbc_u128 *count,
+                          void *stream);
+/* The current count and edge number (nnz may be NULL). */
+sbc_status sbc_dyn_count(const sbc_dyn *d, sbc_u128 *count, int64_t *nnz);
+sbc_status sbc_dyn_destroy(sbc_dyn *d);
+/* H(u, v) of the graph in the given host CSR for edge (u, v) with sign `sign`
+ * (the edge itself need not be present), host only: writes its row and column
+ * numbers and edge number; with h_offsets non-NULL also its CSR (n_l + 1
+ * offsets; h_cols of `capacity` entries, SBC_E_INVAL when it holds fewer than
+ * the edges). Rows follow Gamma(v) - {u} and columns Gamma(u) - {v} in
+ * increasing vertex id. */
+sbc_status sbc_edge_local_graph(int64_t n_u, int64_t n_v, int64_t nnz, const int64_t *row_offsets,
+                                const int32_t *cols, const int8_t *signs, int64_t u, int64_t v,
+                                int8_t sign, int64_t *n_l, int64_t *n_r, int64_t *h_nnz,
+                                int64_t *h_offsets, int32_t *h_cols, int64_t capacity);
+
 const char *sbc_last_error(void);
 
 /* Library version string. */

@@ -544,3 +544,105 @@ def graph_from_synth(g, device: bool = False, sign_bits: bool = False, stream=No
     return sbc_graph_create(g.n_u, g.n_v, np.ascontiguousarray(g.offsets),
                             np.ascontiguousarray(g.cols), np.ascontiguousarray(signs),
                             sign_bits=sign_bits, stream=stream)
+
+
+# ---- dynamic graphs: a count kept exact under edge updates
+
+SBC_DYN_INSERT, SBC_DYN_DELETE, SBC_DYN_SET_SIGN = 0, 1, 2
+
+_declare("sbc_dyn_create", ctypes.c_int,
+         [ctypes.POINTER(_vp), _i64, _i64, _i64, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp])
+_declare("sbc_dyn_update", ctypes.c_int,
+         [_vp, ctypes.c_int, _i64, _i64, ctypes.c_int8, ctypes.POINTER(U128), _vp])
+_declare("sbc_dyn_count", ctypes.c_int, [_vp, ctypes.POINTER(U128), ctypes.POINTER(_i64)])
+_declare("sbc_dyn_destroy", ctypes.c_int, [_vp])
+_declare("sbc_edge_local_graph", ctypes.c_int,
+         [_i64, _i64, _i64, _vp, _vp, _vp, _i64, _i64, ctypes.c_int8, ctypes.POINTER(_i64),
+          ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp, _vp, _i64])
+
+
+def _host_csr(n_u, offsets, cols, signs):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    col = np.ascontiguousarray(cols, dtype=np.int32)
+    sgn = np.ascontiguousarray(signs, dtype=np.int8)
+    if off.shape[0] != n_u + 1 or col.shape[0] != sgn.shape[0]:
+        raise ValueError("CSR arrays of inconsistent lengths")
+    return off, col, sgn
+
+
+class Dynamic:
+    """A balanced (p,q) count (p, q in [3, 8]) kept exact while edges are
+    inserted, deleted or change sign (sbc_dyn_*). Each update counts the
+    balanced bicliques through the edge on the GPU. Use as a context manager
+    or call close()."""
+
+    def __init__(self, n_u: int, n_v: int, offsets, cols, signs, p: int, q: int, stream=None):
+        off, col, sgn = _host_csr(n_u, offsets, cols, signs)
+        h = _vp()
+        _check(lib.sbc_dyn_create(ctypes.byref(h), n_u, n_v, int(col.shape[0]), off.ctypes.data,
+                                  col.ctypes.data, sgn.ctypes.data, p, q, _stream_ptr(stream)))
+        self.h = h.value
+        self.p, self.q = p, q
+
+    @classmethod
+    def from_synth(cls, g, p: int, q: int, stream=None) -> "Dynamic":
+        return cls(g.n_u, g.n_v, g.offsets, g.cols, g.signs, p, q, stream)
+
+    def _update(self, op: int, u: int, v: int, sign: int, stream) -> int:
+        out = U128()
+        _check(lib.sbc_dyn_update(self.h, op, u, v, sign, ctypes.byref(out), _stream_ptr(stream)))
+        return out.value()
+
+    def insert(self, u: int, v: int, sign: int, stream=None) -> int:
+        """Add edge (u, v) with sign +1 / -1; returns the new count."""
+        return self._update(SBC_DYN_INSERT, u, v, sign, stream)
+
+    def delete(self, u: int, v: int, stream=None) -> int:
+        """Remove edge (u, v); returns the new count."""
+        return self._update(SBC_DYN_DELETE, u, v, 1, stream)
+
+    def set_sign(self, u: int, v: int, sign: int, stream=None) -> int:
+        """Give edge (u, v) the sign +1 / -1; returns the new count."""
+        return self._update(SBC_DYN_SET_SIGN, u, v, sign, stream)
+
+    def count(self) -> int:
+        out, nnz = U128(), _i64()
+        _check(lib.sbc_dyn_count(self.h, ctypes.byref(out), ctypes.byref(nnz)))
+        return out.value()
+
+    def edges(self) -> int:
+        out, nnz = U128(), _i64()
+        _check(lib.sbc_dyn_count(self.h, ctypes.byref(out), ctypes.byref(nnz)))
+        return nnz.value
+
+    def close(self):
+        if self.h:
+            lib.sbc_dyn_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def edge_local_graph(n_u: int, n_v: int, offsets, cols, signs, u: int, v: int, sign: int):
+    """H(u, v) of sbc_edge_local_graph (host only): (n_l, n_r, offsets, cols)
+    of the graph whose complete (p-1, q-1) subgraphs are the balanced
+    (p,q)-bicliques through edge (u, v) with sign `sign`."""
+    off, col, sgn = _host_csr(n_u, offsets, cols, signs)
+    n_l, n_r, nnz = _i64(), _i64(), _i64()
+    args = (n_u, n_v, int(col.shape[0]), off.ctypes.data, col.ctypes.data, sgn.ctypes.data, u, v,
+            sign, ctypes.byref(n_l), ctypes.byref(n_r), ctypes.byref(nnz))
+    _check(lib.sbc_edge_local_graph(*args, None, None, 0))
+    h_off = np.zeros(n_l.value + 1, dtype=np.int64)
+    h_col = np.zeros(max(nnz.value, 1), dtype=np.int32)
+    _check(lib.sbc_edge_local_graph(*args, h_off.ctypes.data, h_col.ctypes.data, h_col.shape[0]))
+    return n_l.value, n_r.value, h_off, h_col[:nnz.value]
