@@ -391,7 +391,7 @@ sbc_status sbc_measure_alu_rates(double *popc_per_s, double *lop3_per_s, void *s
  * there, sorted per vertex) and counted by the GPU kernels (its balanced
  * (p-1, q-1) count with every sign positive); p and q are in [3, 8].
  */
-typedef struct sbc_dyn sbc_dyn; /* opaque, owned by the caller */
+typedef struct sbc_dyn sbc_dyn; /* opaque, owned by the caller; one thread at a time per handle */
 #define SBC_DYN_INSERT 0   /* add edge (u, v) with `sign`; the edge must be absent */
 #define SBC_DYN_DELETE 1   /* remove edge (u, v); it must be present (`sign` unused) */
 #define SBC_DYN_SET_SIGN 2 /* give the present edge (u, v) the sign `sign` */
