@@ -253,6 +253,74 @@ def medium_leg(sbc, torch, args):
                          for i, (p, q) in enumerate(pqs)}}
 
 
+def dynamic_leg(sbc, torch, args):
+    """Exact counts under single-edge updates (sbc_dyn_*) on the 2M-edge
+    graph, (3,3): latency of random insertions, each undone by deleting the
+    edge (the count must return to the start), of sign changes of present
+    edges (each undone), and of updates (insertion or sign change) of the
+    pairs of the eight highest-degree vertices of each side."""
+    g = load_workload("plain-200k-100k-2M")
+    rng = np.random.default_rng(17)
+    u_all, v_all, s_all = g.edges()
+    keys = np.sort(u_all.astype(np.int64) * g.n_v + v_all.astype(np.int64))
+
+    def absent(u, v):
+        k = u * g.n_v + v
+        i = int(np.searchsorted(keys, k))
+        return i == keys.shape[0] or int(keys[i]) != k
+
+    t0 = time.perf_counter()
+    d = sbc.Dynamic.from_synth(g, 3, 3)
+    create_s = time.perf_counter() - t0
+    try:
+        base = d.count()
+        ins, dele, flip, hub = [], [], [], []
+        n = args.dyn_updates
+        while len(ins) < n:
+            u, v = int(rng.integers(g.n_u)), int(rng.integers(g.n_v))
+            if not absent(u, v):
+                continue
+            t = time.perf_counter()
+            d.insert(u, v, int(rng.choice([-1, 1])))
+            ins.append(time.perf_counter() - t)
+            t = time.perf_counter()
+            c = d.delete(u, v)
+            dele.append(time.perf_counter() - t)
+            if c != base:
+                raise AssertionError(f"count {c} after undoing an insertion, expected {base}")
+        for e in rng.choice(u_all.shape[0], size=max(1, n // 4), replace=False).tolist():
+            u, v, s = int(u_all[e]), int(v_all[e]), int(s_all[e])
+            t = time.perf_counter()
+            d.set_sign(u, v, -s)
+            flip.append(time.perf_counter() - t)
+            if d.set_sign(u, v, s) != base:
+                raise AssertionError("count changed after undoing a sign change")
+        hubs_u = np.argsort(-np.diff(g.offsets))[:8].tolist()
+        hubs_v = np.argsort(-np.bincount(g.cols, minlength=g.n_v))[:8].tolist()
+        sign_of = dict(zip((u_all * g.n_v + v_all).tolist(), s_all.tolist())) if hubs_u else {}
+        for u in hubs_u:
+            for v in hubs_v:
+                t = time.perf_counter()
+                if absent(u, v):
+                    d.insert(u, v, 1)
+                    hub.append(time.perf_counter() - t)
+                    undone = d.delete(u, v)
+                else:
+                    s = int(sign_of[u * g.n_v + v])
+                    d.set_sign(u, v, -s)
+                    hub.append(time.perf_counter() - t)
+                    undone = d.set_sign(u, v, s)
+                if undone != base:
+                    raise AssertionError("count changed after undoing a hub update")
+    finally:
+        d.close()
+    ms = lambda x: {"median_ms": 1e3 * float(np.median(x)), "p99_ms": 1e3 * float(np.percentile(x, 99)),
+                    "max_ms": 1e3 * float(np.max(x)), "n": len(x)} if x else None
+    return {"workload": "plain-200k-100k-2M", "pq": "(3,3)", "create_s": create_s, "count": base,
+            "insert": ms(ins), "delete": ms(dele), "set_sign": ms(flip), "hub_updates": ms(hub),
+            "exact": "every update undone returned the count to its start"}
+
+
 def batch_leg(sbc, torch, args):
     """Graphs/s for B independent graphs of the 10,000-graph batch recipe:
     plain one-count-per-graph path, one batched count (sbc_count_batch), a
@@ -607,11 +675,13 @@ def run_ours(args):
                          f"{dt:.1f} s; graph lists built once beforehand)",
                "seconds_to_exact_33_estimate": dt / args.cpu_frac}
 
-    medium = batch = serve = sweep = None
+    medium = batch = serve = sweep = dyn = None
     if rank == 0 and ws == 1 and args.pq_sweep:
         sweep = _leg(pq_sweep_leg, sbc, torch, args)
     if rank == 0 and ws == 1 and not args.no_medium:
         medium = _leg(medium_leg, sbc, torch, args)
+    if rank == 0 and ws == 1 and args.dyn_updates > 0:
+        dyn = _leg(dynamic_leg, sbc, torch, args)
     if rank == 0 and ws == 1 and args.batch_graphs > 0:
         batch = _leg(batch_leg, sbc, torch, args)
     if rank == 0 and ws == 1 and args.serve_requests > 0:
@@ -640,7 +710,7 @@ def run_ours(args):
             "roofline": roof, "roofline_kernels": roofs, "peak_source": peak_kind,
             "alu_rates": alu, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
             "cpu_baseline": cpu, "medium": medium, "batch": batch, "serve": serve,
-            "pq_sweep": sweep,
+            "pq_sweep": sweep, "dynamic": dyn,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -684,6 +754,8 @@ def main():
     ap.add_argument("--no-medium", action="store_true", help="skip the 2M-edge leg")
     ap.add_argument("--pq-sweep", action="store_true",
                     help="also time p in {3,4,5} x q in {3..7} on the 20k- and 2M-edge graphs")
+    ap.add_argument("--dyn-updates", type=int, default=200,
+                    help="random edge insertions of the dynamic-count leg (0: skip the leg)")
     ap.add_argument("--batch-graphs", type=int, default=10000,
                     help="graphs of the batch leg (0 skips it; the full recipe is 10000)")
     ap.add_argument("--serve-graphs", type=int, default=500)

@@ -16,8 +16,9 @@
 // compute. p and q must be at least 3 so that p-1 and q-1 are valid sizes.
 //
 // The adjacency is kept on the host (sorted lists per vertex, the mutable
-// state of the graph); H is assembled on the host by one merge of Gamma(w)
-// with Gamma(u) per w in Gamma(v), then uploaded and counted on the GPU.
+// state of the graph); H is assembled on the host from Gamma(w) and Gamma(u)
+// for every w in Gamma(v) (a merge, or binary searches into Gamma(u) when
+// Gamma(w) is much shorter), then uploaded and counted on the GPU.
 #include <algorithm>
 #include <memory>
 #include <utility>
@@ -59,17 +60,27 @@ Csr local_graph(const std::vector<AdjList> &adj_u, const std::vector<AdjList> &a
         if (w == u) continue;
         const int8_t s_wv = wv.second;
         const AdjList &Nw = adj_u[w];
-        size_t i = 0, j = 0;  // merge Gamma(u) with Gamma(w), both by V id
-        while (i < Nu.size() && j < Nw.size()) {
-            if (Nu[i].first < Nw[j].first) {
-                i++;
-            } else if (Nw[j].first < Nu[i].first) {
-                j++;
-            } else {
-                if (col_of[i] >= 0 && s_uv * Nu[i].second * s_wv * Nw[j].second == 1)
-                    h.col.push_back(col_of[i]);
-                i++;
-                j++;
+        auto keep = [&](size_t i, int8_t s_wx) {
+            if (col_of[i] >= 0 && s_uv * Nu[i].second * s_wv * s_wx == 1) h.col.push_back(col_of[i]);
+        };
+        if (8 * Nw.size() < Nu.size()) {
+            // Gamma(w) much shorter: look each of its vertices up in Gamma(u)
+            for (const auto &xs : Nw) {
+                auto it = std::lower_bound(Nu.begin(), Nu.end(), std::make_pair(xs.first, (int8_t)-128));
+                if (it != Nu.end() && it->first == xs.first) keep((size_t)(it - Nu.begin()), xs.second);
+            }
+        } else {
+            size_t i = 0, j = 0;  // merge Gamma(u) with Gamma(w), both by V id
+            while (i < Nu.size() && j < Nw.size()) {
+                if (Nu[i].first < Nw[j].first) {
+                    i++;
+                } else if (Nw[j].first < Nu[i].first) {
+                    j++;
+                } else {
+                    keep(i, Nw[j].second);
+                    i++;
+                    j++;
+                }
             }
         }
         h.off.push_back((int64_t)h.col.size());

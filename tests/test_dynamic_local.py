@@ -78,6 +78,36 @@ def test_updates_change_the_count_by_the_local_count(sbc, p, q):
                                       local_count(sbc, g, a, b, s, p, q))
 
 
+def test_updates_at_a_high_degree_vertex(sbc):
+    """u adjacent to most of V and its partners of low degree: the local graph
+    is assembled by lookups into Gamma(u) rather than merges."""
+    rng = np.random.default_rng(77)
+    m, n = 30, 220
+    d = {}
+    for b in range(n):
+        if rng.random() < 0.9:
+            d[(0, b)] = int(rng.choice([-1, 1]))
+    for a in range(1, m):
+        for b in rng.choice(n, size=int(rng.integers(3, 12)), replace=False).tolist():
+            d[(a, b)] = int(rng.choice([-1, 1]))
+    for b in range(0, n, 7):  # a few columns shared by many rows
+        for a in range(1, m, 2):
+            d[(a, b)] = d.get((a, b), 1)
+    g = from_dict(m, n, d)
+    for p, q in [(3, 3), (3, 4), (4, 3)]:
+        base = oracle.count(g, p, q)
+        present = [k for k in d if k[0] == 0]
+        for a, b in present[:6]:
+            s = d[(a, b)]
+            rest = {x: y for x, y in d.items() if x != (a, b)}
+            assert base - oracle.count(from_dict(m, n, rest), p, q) == local_count(sbc, g, a, b, s, p, q)
+        absent = [b for b in range(n) if (0, b) not in d]
+        for b in absent[:4]:
+            for s in (1, -1):
+                after = oracle.count(from_dict(m, n, {**d, (0, b): s}), p, q)
+                assert after - base == local_count(sbc, g, 0, b, s, p, q)
+
+
 def test_local_graph_layout(sbc):
     """u = 0 with neighbours {0, 1, 2}; v = 1 with neighbours {0, 1, 3};
     rows are Gamma(v) - {u} = (1, 3), columns Gamma(u) - {v} = (0, 2)."""
