@@ -298,8 +298,11 @@ def dynamic_leg(sbc, torch, args):
         hubs_u = np.argsort(-np.diff(g.offsets))[:8].tolist()
         hubs_v = np.argsort(-np.bincount(g.cols, minlength=g.n_v))[:8].tolist()
         sign_of = dict(zip((u_all * g.n_v + v_all).tolist(), s_all.tolist())) if hubs_u else {}
+        t_hub = time.perf_counter()
         for u in hubs_u:
             for v in hubs_v:
+                if time.perf_counter() - t_hub > 20.0:  # bounded wall time for the leg
+                    break
                 t = time.perf_counter()
                 if absent(u, v):
                     d.insert(u, v, 1)
