@@ -672,11 +672,16 @@ def run_ours(args):
         p, q = PQ[0]
         with oracle.Prepared(g, side) as prep:
             tup, dt, na, cores = oracle_sample(prep, g, side, p, q, args.cpu_frac, 7)
+            # the same oracle on one thread, on a tenth of the sample
+            tup1, dt1, na1, _ = oracle_sample(prep, g, side, p, q, args.cpu_frac / 10, 8, threads=1)
         cpu = {"value": tup / dt, "unit": "anchor tuples/s", "cores": cores, "kind": "oracle",
                "sample": f"({p},{q}) on a seeded random {args.cpu_frac:.3%} sample of "
                          f"{'U' if side == 0 else 'V'} anchors ({na} anchors, {tup} tuples, "
                          f"{dt:.1f} s; graph lists built once beforehand)",
-               "seconds_to_exact_33_estimate": dt / args.cpu_frac}
+               "seconds_to_exact_33_estimate": dt / args.cpu_frac,
+               "one_thread": {"value": tup1 / dt1 if dt1 > 0 else None, "cores": 1,
+                              "sample": f"{args.cpu_frac / 10:.4%} of the anchors "
+                                        f"({na1} anchors, {tup1} tuples, {dt1:.1f} s)"}}
 
     medium = batch = serve = sweep = dyn = None
     if rank == 0 and ws == 1 and args.pq_sweep:
