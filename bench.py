@@ -512,6 +512,9 @@ def run_ours(args):
 
     dev = torch.cuda.current_device()
     g = load_workload()
+    import sbc_synth
+
+    input_digest = sbc_synth.digest(g)  # compare with tests/golden/input_digests.txt
     stream = torch.cuda.Stream()
     off = torch.from_numpy(g.offsets).cuda()
     col = torch.from_numpy(g.cols).cuda()
@@ -705,6 +708,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "pq": "+".join(f"({p},{q})" for p, q in PQ),
                        "n_u": g.n_u, "n_v": g.n_v, "edges": g.m,
+                       "input_sha256": input_digest,
                        "l2": "inputs (1.1 GB on the device) larger than L2, and flushed "
                              "between steps (512 MiB write)",
                        "parallelism": f"anchor shards x{ws}" if ws > 1 else "1 GPU"},

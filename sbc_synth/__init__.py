@@ -306,3 +306,17 @@ def dense_factions_wide() -> SignedBipartite:
     positions (three 128-position blocks), the typical tensor-core tile of
     the 60M-edge graph's (3,3) count."""
     return dense_factions(n=800, seed=6)
+
+
+def digest(g: SignedBipartite) -> str:
+    """SHA-256 of a graph's content: n_u, n_v (int64), offsets (int64), cols
+    (int32), signs (int8), little-endian, in that order. Equal digests mean
+    the generator produced the same graph (on any machine)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    h.update(np.array([g.n_u, g.n_v], dtype="<i8").tobytes())
+    h.update(np.ascontiguousarray(g.offsets, dtype="<i8").tobytes())
+    h.update(np.ascontiguousarray(g.cols, dtype="<i4").tobytes())
+    h.update(np.ascontiguousarray(g.signs, dtype="i1").tobytes())
+    return h.hexdigest()
