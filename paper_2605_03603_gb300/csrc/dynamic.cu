@@ -138,7 +138,8 @@ void build_adjacency(int64_t n_u, int64_t n_v, int64_t nnz, const int64_t *off, 
         fail(SBC_E_INVAL, "vertex counts out of range");
     if ((n_u > 0 || nnz > 0) && (!off || (nnz > 0 && (!col || !sgn))))
         fail(SBC_E_INVAL, "NULL CSR array");
-    if (n_u > 0 && (off[0] != 0 || off[n_u] != nnz)) fail(SBC_E_GRAPH, "offsets do not span the edges");
+    if (nnz < 0 || (n_u == 0 && nnz != 0) || (n_u > 0 && (off[0] != 0 || off[n_u] != nnz)))
+        fail(SBC_E_GRAPH, "offsets do not span the edges");
     adj_u.assign((size_t)n_u, AdjList());
     adj_v.assign((size_t)n_v, AdjList());
     for (int64_t x = 0; x < n_u; x++) {
