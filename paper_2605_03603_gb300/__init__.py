@@ -646,3 +646,53 @@ def edge_local_graph(n_u: int, n_v: int, offsets, cols, signs, u: int, v: int, s
     h_col = np.zeros(max(nnz.value, 1), dtype=np.int32)
     _check(lib.sbc_edge_local_graph(*args, h_off.ctypes.data, h_col.ctypes.data, h_col.shape[0]))
     return n_l.value, n_r.value, h_off, h_col[:nnz.value]
+
+
+# ---- checkpoint / resume of long counts
+
+def sbc_count_resumable(g: Graph, p: int, q: int, shards: int, state_path: str,
+                        anchor_side: int = SBC_SIDE_AUTO, stream=None, count_fn=None) -> int:
+    """The exact count taken in `shards` anchor shards (sbc_count_ex's
+    shard / shard_count: anchors of rank r with r % shards == i form shard i),
+    each shard's exact partial sum recorded in the JSON file `state_path`
+    (replaced atomically) as soon as it is known. A later call with the same
+    graph shape, (p, q), shard number and side resumes after the shards
+    already recorded; a state file of another count raises ValueError.
+    count_fn (tests only) replaces sbc_count_ex."""
+    import json
+    import os
+
+    count_fn = count_fn or sbc_count_ex
+    key = {"n_u": int(g.n_u), "n_v": int(g.n_v), "nnz": int(g.nnz), "p": p, "q": q,
+           "shards": int(shards)}
+    state = {**key, "side": None if anchor_side == SBC_SIDE_AUTO else int(anchor_side),
+             "done": [], "partial": "0"}
+    if os.path.exists(state_path):
+        with open(state_path) as f:
+            old = json.load(f)
+        if any(old.get(k) != v for k, v in key.items()) or (
+                anchor_side != SBC_SIDE_AUTO and old.get("side") not in (None, anchor_side)):
+            raise ValueError(f"{state_path} records another count: {old}")
+        state = old
+    done, total = set(state["done"]), int(state["partial"])
+
+    def save():
+        tmp = f"{state_path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(state, f)
+        os.replace(tmp, state_path)
+
+    for i in range(int(shards)):
+        if i in done:
+            continue
+        side = SBC_SIDE_AUTO if state["side"] is None else state["side"]
+        c, st, _ = count_fn(g, p, q, anchor_side=side, shard=i, shard_count=int(shards),
+                            stream=stream)
+        if state["side"] is None:
+            state["side"] = int(st["anchor_side"])
+        total += int(c)
+        done.add(i)
+        state["done"] = sorted(done)
+        state["partial"] = str(total)
+        save()
+    return total

@@ -264,6 +264,25 @@ def test_sharding_partitions_anchors(sbc, small):
     assert sum(parts) == want
 
 
+def test_resumable_count_after_an_interruption(sbc, small, tmp_path):
+    """sbc_count_resumable: a count interrupted after two of five shards and
+    resumed from its state file gives the oracle's total."""
+    want = oracle.count(small, 3, 3)
+    path = str(tmp_path / "count.json")
+    calls = {"n": 0}
+
+    def flaky(*a, **k):
+        calls["n"] += 1
+        if calls["n"] == 3:
+            raise RuntimeError("interrupted")
+        return sbc.sbc_count_ex(*a, **k)
+
+    with sbc.graph_from_synth(small) as h:
+        with pytest.raises(RuntimeError):
+            sbc.sbc_count_resumable(h, 3, 3, 5, path, count_fn=flaky)
+        assert sbc.sbc_count_resumable(h, 3, 3, 5, path) == want
+
+
 # ---------------------------------------------------------------- both sides
 
 @pytest.mark.parametrize("method", ["candidate", "position"])
