@@ -66,3 +66,19 @@ def test_autotune_rejects_empty_batch_on_host(lib):
     out = (ctypes.c_int32 * 4)()
     assert lib.sbc_autotune(None, 0, 3, 3, 0, out, None) == 1  # SBC_E_INVAL
     assert lib.sbc_autotune(None, 0, 3, 3, 0, None, None) == 1
+
+
+def test_plain_c_client(lib, tmp_path):
+    """sbc.h compiles as C and a C program linked against libsbc.so runs the
+    host-side paths (argument and graph errors, a local graph)."""
+    import subprocess
+
+    path = lib._name
+    exe = str(tmp_path / "abi_client")
+    libdir = os.path.dirname(path)
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "abi_client.c"), "-o", exe,
+                           path, f"-Wl,-rpath,{libdir}"])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "ok"
