@@ -36,6 +36,13 @@
  *    thread; a graph must be used on the device it was created on.
  *  - Device memory comes from cudaMallocAsync on the call's stream unless an
  *    allocator is installed with sbc_set_allocator.
+ *  - Environment variables read at each count: SBC_DEBUG=1 (device
+ *    self-checks, as SBC_COUNT_CHECK), SBC_POS_NODE_COST (unit of the
+ *    position-side cost model), SBC_TC_MIN_CANDIDATES (candidates an anchor
+ *    needs for the tensor-core pair step), SBC_POOL_BUDGET_KB (candidate-mask
+ *    pool per anchor group); for tests only, SBC_HASH_SLOTS_CAP (2-hop table
+ *    size cap, to make tables overflow) and SBC_TWOHOP_WINDOW (wedges of a
+ *    one-window anchor, to force the bucketed 2-hop strategy on small graphs).
  */
 #ifndef SBC_H
 #define SBC_H
